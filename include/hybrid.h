@@ -1,0 +1,196 @@
+/*
+ * hybrid.h -- C-ABI of the GB300 hybrid tree force path.
+ *
+ * The method (Watanabe & Nakasato, "GPU accelerated Hybrid Tree Algorithm for
+ * Collision-less N-body Simulations") splits softened gravity, Eq. (1)-(2),
+ * into a hard part F*K(r) and a soft part F*(1-K(r)) with the DLL kernel K of
+ * Eq. (10) (Eq. 7-9). The soft part comes from a Barnes-Hut octree
+ * (Sec. II-B), the hard part from direct summation over neighbours within R2
+ * (found with the test of Eq. 15), and each part is advanced by its own
+ * leap-frog, Eq. (3)-(4), with dt_soft = n_hard * dt_hard (Sec. II-C).
+ *
+ * Conventions for every call:
+ *  - All particle arrays are DEVICE pointers owned by the caller (CUDA
+ *    allocations, e.g. torch tensors), structure-of-arrays, length n.
+ *  - Work is enqueued on the context's stream and is asynchronous unless a
+ *    call says otherwise. Device-side failures (capacity, timeout) are
+ *    reported by the next call that synchronises (hybrid_step,
+ *    hybrid_step_batched, hybrid_sync).
+ *  - Argument errors return HYBRID_EINVAL before anything is enqueued.
+ *  - Nothing throws across this boundary; hybrid_last_error() gives the text
+ *    of the last failure on a context.
+ *  - The state is kept in Morton (key) order: a tree build re-sorts x, v, m
+ *    and id in place (the particle sort of Sec. III-A1).
+ */
+#ifndef HYBRID_H
+#define HYBRID_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYBRID_OK = 0,
+    HYBRID_EINVAL = 1,     /* bad argument: nothing was enqueued */
+    HYBRID_ENOMEM = 2,     /* device allocation failed */
+    HYBRID_ECUDA = 3,      /* a CUDA runtime call failed */
+    HYBRID_ECAPACITY = 4,  /* an internal buffer overflowed and could not be regrown */
+    HYBRID_ETIMEOUT = 5    /* a bounded device-side wait gave up */
+} hybrid_status;
+
+/* Method parameters (Sec. II; Sec. IV-A gives the paper's values).
+ * G        gravitational constant (Eq. 2)
+ * eps      softening length (Eq. 2), >= 0
+ * theta    opening angle for mac = 0: a cell is opened when r < l/theta + delta
+ *          (l cell side, delta offset of the centre of mass from the cell
+ *          centre); theta = 0 opens every cell (direct summation)
+ * R1, R2   transition radii of K (Eq. 10); 0 <= R1 < R2, or R1 = R2 = 0 for
+ *          no hard part (K = 0)
+ * dt_soft  soft time step dt_s; the hard step is dt_soft / n_hard (Sec. II-C)
+ * a_err    accuracy parameter of the absolute MAC (Eq. 5), used when mac = 1
+ * n_hard   n >= 1: hard sub-steps per soft step
+ * n_leaf   a cell splits while it holds more than n_leaf particles (Sec. II-B)
+ * n_crit   sink groups are the first cells holding <= n_crit particles (or
+ *          leaves): the grouped form of the n_vec sinks of Sec. III-A2, Eq. (11)
+ * precision 0: all pair arithmetic in FP64; 1: FP32 pair arithmetic on
+ *          coordinates relative to each sink group (state stays FP64)
+ * mac      0: opening angle theta; 1: absolute MAC with a_err (Eq. 5-6)
+ * threads_per_group, tile_depth: tuning knobs, 0 = built-in defaults */
+typedef struct {
+    double G, eps, theta, R1, R2, dt_soft, a_err;
+    int32_t n_hard, n_leaf, n_crit;
+    int32_t precision;
+    int32_t mac;
+    int32_t threads_per_group;
+    int32_t tile_depth;
+} hybrid_params;
+
+/* One independent system. Arrays are device pointers of length n.
+ * x..m      FP64 state (positions, velocities, masses), caller-owned
+ * id        optional int32 labels permuted together with the state (NULL ok)
+ * ax_s..az_h accelerations: soft (s) and hard (h); float when the context's
+ *          precision is 1, double when 0. hybrid_step reads them as the
+ *          forces at the current positions when forces_valid != 0 and writes
+ *          the forces at the final positions.
+ * params   optional per-system override of G, eps, theta, R1, R2, dt_soft,
+ *          a_err and mac (the other fields are taken from the context); NULL
+ *          uses the context's parameters.
+ * forces_valid in/out: set to 1 by every call that leaves the accelerations
+ *          consistent with the positions, to 0 by hybrid_build_tree. */
+typedef struct {
+    int64_t n;
+    double *x, *y, *z, *vx, *vy, *vz, *m;
+    int32_t *id;
+    void *ax_s, *ay_s, *az_s, *ax_h, *ay_h, *az_h;
+    const hybrid_params *params;
+    int32_t forces_valid;
+} hybrid_system;
+
+typedef struct hybrid_ctx hybrid_ctx;
+
+/* Creates a context bound to the current CUDA device and to `stream`
+ * (a cudaStream_t; NULL = the legacy default stream). Validates p (EINVAL). */
+hybrid_status hybrid_create(hybrid_ctx **ctx, const hybrid_params *p, void *stream);
+
+/* Frees every device buffer the context owns. NULL is accepted. */
+hybrid_status hybrid_destroy(hybrid_ctx *ctx);
+
+/* Sec. III-A1: root cell, Morton keys, stable key sort, the particle data
+ * gathered into key order, level-wise octree split (n_leaf), cell mass and
+ * centre of mass (Sec. II-B), b_max, B2 and the MAC radius (Eq. 5-6), and the
+ * sink groups. Re-sorts x, v, m and id of `sys` in place and keeps the tree
+ * in the context for the force calls; sets sys->forces_valid = 0. */
+hybrid_status hybrid_build_tree(hybrid_ctx *ctx, hybrid_system *sys);
+
+/* Soft force (Eq. 9): for every sink group, a tree walk from the root
+ * (Sec. II-B traversal; Eq. 11 distance to the group box) that takes a cell
+ * whole when r >= r_b and r >= R2 + b_max (Eq. 15), else opens it; then
+ * a_soft = sum over taken cells of F + sum over listed particles of
+ * F*(1 - K). Uses the tree and positions of the last hybrid_build_tree on
+ * this context; writes ax_s, ay_s, az_s. */
+hybrid_status hybrid_soft_force(hybrid_ctx *ctx, hybrid_system *sys);
+
+/* Hard force (Eq. 8): neighbour walk keeping cells with r < R2 + b_max
+ * (Eq. 15), then a_hard = sum over their particles of F*K(r) (Eq. 10).
+ * Same tree as hybrid_soft_force; writes ax_h, ay_h, az_h. */
+hybrid_status hybrid_hard_force(hybrid_ctx *ctx, hybrid_system *sys);
+
+/* Kick, Eq. (3): v <- v + dt * a, with a the soft (which = 0) or the hard
+ * (which = 1) acceleration of sys. */
+hybrid_status hybrid_kick(hybrid_ctx *ctx, hybrid_system *sys, int which, double dt);
+
+/* Drift, Eq. (4): x <- x + dt * v. */
+hybrid_status hybrid_drift(hybrid_ctx *ctx, hybrid_system *sys, double dt);
+
+/* n_soft_steps soft steps of the hybrid scheme (Sec. II-C), each
+ *   K_s(dt_s/2); n_hard x [K_h(dt_h/2); D(dt_h); tree build; hard force
+ *   (and at the last sub-step also the soft force); K_h(dt_h/2)]; K_s(dt_s/2)
+ * i.e. one soft-step and n_hard - 1 hard-steps per dt_s. Forces at the start
+ * are computed first when sys->forces_valid == 0. Synchronises the stream at
+ * the end and returns any device-side failure. */
+hybrid_status hybrid_step(hybrid_ctx *ctx, hybrid_system *sys, int n_soft_steps);
+
+/* The same for n_sys independent systems of uneven size, processed together:
+ * every kernel launch covers all systems. All systems share n_hard, n_leaf,
+ * n_crit and precision; their other parameters may differ (params). */
+hybrid_status hybrid_step_batched(hybrid_ctx *ctx, hybrid_system *sys, int n_sys, int n_soft_steps);
+
+/* Copies the permutation of the last call into dev_perm (device int32, length
+ * = total particles of that call): dev_perm[k] = index, in that call's input
+ * order within its system, of the particle now at position k. */
+hybrid_status hybrid_get_perm(hybrid_ctx *ctx, int32_t *dev_perm);
+
+/* Waits for the context's stream and returns the first device-side failure
+ * recorded since the last check (and clears it). */
+hybrid_status hybrid_sync(hybrid_ctx *ctx);
+
+/* Text of the last failure on ctx ("" if none). Valid until the next call. */
+const char *hybrid_last_error(hybrid_ctx *ctx);
+
+/* ---- inspection (tests and tuning; not needed to run a simulation) ---- */
+
+/* Tree of the last build: node count, group count, and host copies.
+ * Sizes: the caller passes arrays of length >= the counts; any pointer may be
+ * NULL. Nodes are in breadth-first order over all systems: by level, then
+ * system, then key. Groups are in particle order. level/nchild are int32,
+ * first/count/child/parent int64 (child = -1 for a leaf, parent = -1 for a
+ * root); moments are 13 doubles per node (M, cx, cy, cz, b_max, B2, delta,
+ * side, ox, oy, oz, r_b, 0). keys (uint64) are in sorted order. */
+hybrid_status hybrid_tree_info(hybrid_ctx *ctx, int64_t *n_nodes, int64_t *n_groups);
+hybrid_status hybrid_tree_copy(hybrid_ctx *ctx, uint64_t *keys, int32_t *level, int64_t *first, int64_t *count,
+                               int64_t *child, int32_t *nchild, int64_t *parent, double *moments,
+                               int64_t *group_node, double *group_lo, double *group_hi);
+
+/* Interaction lists of the last force walk, host copies. mode bit 0: the
+ * soft lists (cells, particles), bit 1: the hard list. counts: 3 int64 per
+ * group (soft cells, soft particles, hard particles); entries (int64, node or
+ * sorted particle index) back to back per group in that order. Pass
+ * entries = NULL to get the counts only. */
+hybrid_status hybrid_lists_copy(hybrid_ctx *ctx, int64_t *counts, int64_t *entries, int64_t cap_entries);
+
+/* Sink-source pairs evaluated by the soft and hard pair kernels of the last
+ * force evaluation (sum over groups of |group| x list length). */
+hybrid_status hybrid_interactions(hybrid_ctx *ctx, int64_t *soft, int64_t *hard);
+
+/* Profiling: when enabled, the pair kernels are bracketed by CUDA events on
+ * the context stream. hybrid_profile_read synchronises and returns, per
+ * kernel kind (0 soft pair, 1 hard pair, 2 walk, 3 tree build, 4 kick/drift),
+ * the summed milliseconds and launch count since the last reset. */
+hybrid_status hybrid_profile(hybrid_ctx *ctx, int enable);
+hybrid_status hybrid_profile_read(hybrid_ctx *ctx, int kind, double *ms, int64_t *launches, int reset);
+
+/* Number of kernels this context has launched so far (all kinds). */
+int64_t hybrid_launch_count(hybrid_ctx *ctx);
+
+/* Softened energies (Sec. IV-A "total energy") of a system by direct
+ * summation on the device: kinetic and potential, returned to the host
+ * (synchronises). Uses the context's eps and G (or sys->params). */
+hybrid_status hybrid_energy(hybrid_ctx *ctx, hybrid_system *sys, double *kinetic, double *potential);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HYBRID_H */

@@ -1,0 +1,182 @@
+// hy_internal.cuh -- internal definitions of the CUDA library (context, device
+// tables, kernel launchers). Not a public header; see include/hybrid.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hybrid.h"
+
+namespace hy {
+
+constexpr int LEVELS = 21;                 // 3 x 21 = 63 Morton key bits
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr int RS_WARPS = 8;                // radix sort: 8 warps x 32 lanes x 16 items
+constexpr int RS_IPT = 16;
+constexpr int RS_TILE = RS_WARPS * 32 * RS_IPT;   // 4096 keys per tile
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_IPT = 8;
+constexpr int SCAN_SEG = SCAN_THREADS * SCAN_IPT; // 2048 elements per scan segment
+
+// Per-system parameters on the device (FP64 for the tree/integrator, FP32
+// copies for the pair kernels).
+struct SysParams {
+    double G, eps2, theta, R1, R2, dt_soft, a_err;
+    double R2sq, invdR;            // R2^2, 1/(R2-R1) (0 when there is no hard part)
+    float Gf, eps2f, R2f, R2sqf, invdRf, R2sqlo;   // R2sqf + R2sqlo = R2^2 to ~2^-48
+    int32_t mac, has_hard;
+};
+
+// Root cube of one system: origin lo, side L (a power of two), scale = 2^21/L.
+// The FP32 copies of positions are taken relative to lo and split as
+// x - lo = hi + lo_part with hi on the grid of step u = L / 2^20, so hi is
+// exact in FP32 and the difference of two hi values is exact too.
+struct SysBox {
+    double lo[3];
+    double L;
+    double scale;
+    double u, inv_u;
+    double pad;
+};
+
+// Device status block: first failure wins (atomicCAS on code).
+struct Status {
+    int32_t code;        // hybrid_status of the first failure, 0 = none
+    int32_t where;       // op index at which it happened
+    int64_t need[6];     // [0] nodes, [1] list entries, [2] walk stack entries
+    int64_t counters[4]; // [0] soft interactions, [1] hard interactions
+};
+
+// A tile of at most RS_TILE consecutive particles inside one system.
+struct Chunk {
+    int64_t start;
+    int32_t len;
+    int32_t sys;
+    int32_t first_chunk;   // first chunk of this chunk's system
+    int32_t nchunk;        // chunks of this chunk's system
+};
+
+// Per-group data for the walk and pair kernels.
+struct GroupF {
+    float4 c_hi;       // centre of the member box, hi part; w = half extent x
+    float4 c_lo;       // centre lo part; w = half extent y
+    float2 hz_root;    // x = half extent z; y unused
+};
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Caller arrays of one system (device pointers) and its offset in the batch.
+struct SysIO {
+    double *x[7];
+    int32_t *id;
+    void *as[3], *ah[3];
+    int64_t n, off;
+};
+
+enum ProfKind { PROF_SOFT = 0, PROF_HARD = 1, PROF_WALK = 2, PROF_TREE = 3, PROF_INTEG = 4, PROF_KINDS = 5 };
+
+}  // namespace hy
+
+struct hybrid_ctx {
+    hybrid_params p{};
+    cudaStream_t st = nullptr;
+    int dev = 0, nsm = 0;
+    std::string err;
+    int64_t launches = 0;
+    int op = 0;   // index of the op being enqueued (for failure reports)
+
+    // batch layout of the current call
+    int S = 0;
+    int64_t N = 0;
+    std::vector<int64_t> h_off;                // S + 1
+    std::vector<hy::SysParams> h_sp;
+    std::vector<hy::Chunk> h_chunks;
+    std::vector<hy::SysIO> h_io;
+    int nchunks = 0;
+    bool tree_valid = false, have_soft = false, have_hard = false;
+
+    // capacities
+    int64_t capN = 0, capS = 0, capChunks = 0, capNodes = 0, capGroups = 0, capList = 0, capStack = 0;
+    int walk_warps = 0;
+
+    // device buffers: state (two copies each for the permutation), ids
+    hy::Buf x[7], xa[7], id, ida, orig, origa, psys;
+    hy::Buf acc_s[3], acc_h[3];            // float or double
+    hy::Buf phi, plo, pd;                  // float4 hi/lo (precision 1), double4_32a (precision 0)
+    hy::Buf keys[2], vals[2], hist, blocksum;
+    hy::Buf off_dev, sp_dev, chunks_dev, boxmin, boxmax, box, sysroot;
+    hy::Buf status;
+    // tree
+    hy::Buf lvl, nfirst, ncount, nchild, nnch, nparent, nlevel, ndone, nchtmp, leafof;
+    hy::Buf nM, ncx, ncy, ncz, nB2, nbmax;     // FP64 moments
+    hy::Buf nA, nB, ncrit, ntopo;              // FP32 walk/pair node data
+    hy::Buf nD, nrb, nhr;                      // FP64 walk/pair node data (precision 0)
+    hy::Buf ndelta, nside, norg;               // geometry (inspection + finalize)
+    hy::Buf gflag, gscan, gnode, gfirst, gcount, gsys, gF, glo, ghi, ngroups_dev;
+    // lists
+    hy::Buf lcnt, loff, list, stack, counter, io_dev, energy_dev;
+    int last_walk_mode = 0;
+
+    // profiling
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    double prof_ms[hy::PROF_KINDS] = {0};
+    int64_t prof_n[hy::PROF_KINDS] = {0};
+
+    // host pinned status
+    hy::Status *h_status = nullptr;
+};
+
+namespace hy {
+
+// ---- memory / errors (hybrid_api.cu) ----
+bool ensure(hybrid_ctx *c, Buf &b, size_t bytes);
+void set_err(hybrid_ctx *c, const char *fmt, ...);
+inline Status *status_dev(hybrid_ctx *c) { return (Status *)c->status.p; }
+void prof_begin(hybrid_ctx *c, int kind, cudaEvent_t *e0);
+void prof_end(hybrid_ctx *c, int kind, cudaEvent_t e0);
+
+// ---- scans (scan.cu) ----
+// Exclusive scan of n uint32 values (n from *d_n when d_n != null, else n_host),
+// in place; *d_total (optional) receives the sum. n_max bounds the grid.
+void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total);
+void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total);
+
+// ---- tree (tree.cu) ----
+void launch_box(hybrid_ctx *c);
+void launch_keys_sort_permute(hybrid_ctx *c);
+bool launch_build_levels(hybrid_ctx *c);
+void launch_moments(hybrid_ctx *c);
+void launch_groups(hybrid_ctx *c);
+
+// ---- walk (walk.cu) ----
+void launch_walk(hybrid_ctx *c, int mode);   // mode bit 0 soft, bit 1 hard
+
+// ---- pair kernels (pair.cu) ----
+void launch_pair_soft(hybrid_ctx *c);
+void launch_pair_hard(hybrid_ctx *c);
+
+// ---- integrator and io (integrate.cu) ----
+void launch_copy_in(hybrid_ctx *c, const SysIO *d_io, bool with_acc);
+void launch_copy_out(hybrid_ctx *c, const SysIO *d_io, bool state, bool acc_s, bool acc_h);
+// Applies n <= 4 kicks v <- v + h a_which in order (which 0 soft, 1 hard;
+// mode 0: h = val, 1: h = dt_soft/2, 2: h = (dt_soft/n_hard)/2, per system),
+// then a drift x <- x + dt v (dmode -1: none, 0: dt = dval, 2: dt_soft/n_hard).
+void launch_kick_seq(hybrid_ctx *c, int n, const int *which, const int *mode, const double *val, int dmode,
+                     double dval);
+void launch_kick_ext(hybrid_ctx *c, const hybrid_system *s, int which, double h);
+void launch_drift_ext(hybrid_ctx *c, const hybrid_system *s, double dt);
+void launch_energy(hybrid_ctx *c, double *d_out /* 2*S */);
+
+}  // namespace hy
+
+// kernel launch bookkeeping
+#define HY_LAUNCHED(c) ((c)->launches++)

@@ -1,0 +1,807 @@
+// hybrid_api.cu -- the C-ABI of include/hybrid.h: context, device memory,
+// and the step driver that enqueues the hybrid scheme (Sec. II-C) as a
+// sequence of ops on the context's stream.
+//
+// Recovery from capacity overflow: every kernel returns at once when the
+// device status word holds a failure, so after a failed op nothing later in
+// the sequence has touched the state. The driver then grows the buffer that
+// overflowed and resumes at the tree build of the failed force evaluation
+// (a build re-sorts already sorted particles into the same order, so it can
+// be repeated).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "hy_internal.cuh"
+
+using hy::Buf;
+
+namespace hy {
+
+bool ensure(hybrid_ctx *c, Buf &b, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return true;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t nb = std::max<size_t>(bytes, 256);
+    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        set_err(c, "cudaMalloc of %zu bytes failed", nb);
+        return false;
+    }
+    b.bytes = nb;
+    return true;
+}
+
+void set_err(hybrid_ctx *c, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+}
+
+void prof_begin(hybrid_ctx *c, int kind, cudaEvent_t *e0)
+{
+    (void)kind;
+    *e0 = nullptr;
+    if (!c->prof) return;
+    if (c->ev_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    *e0 = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    cudaEventRecord(*e0, c->st);
+}
+
+void prof_end(hybrid_ctx *c, int kind, cudaEvent_t e0)
+{
+    if (!c->prof || !e0) return;
+    if (c->ev_pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        c->ev_pool.push_back(e);
+    }
+    cudaEvent_t e1 = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    cudaEventRecord(e1, c->st);
+    c->ev_used.push_back({kind, {e0, e1}});
+}
+
+}  // namespace hy
+
+namespace {
+
+using namespace hy;
+
+bool params_ok(const hybrid_params *p, std::string *why)
+{
+    auto bad = [&](const char *m) {
+        if (why) *why = m;
+        return false;
+    };
+    if (!std::isfinite(p->G)) return bad("G must be finite");
+    if (!(p->eps >= 0.0) || !std::isfinite(p->eps)) return bad("eps must be >= 0");
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta)) return bad("theta must be >= 0");
+    const bool no_hard = (p->R1 == 0.0 && p->R2 == 0.0);
+    if (!no_hard && !(p->R1 >= 0.0 && p->R2 > p->R1 && std::isfinite(p->R2)))
+        return bad("need 0 <= R1 < R2, or R1 = R2 = 0");
+    if (!std::isfinite(p->dt_soft)) return bad("dt_soft must be finite");
+    if (p->n_hard < 1) return bad("n_hard must be >= 1");
+    if (p->n_leaf < 1) return bad("n_leaf must be >= 1");
+    if (p->n_crit < 1) return bad("n_crit must be >= 1");
+    if (p->precision != 0 && p->precision != 1) return bad("precision must be 0 or 1");
+    if (p->mac != 0 && p->mac != 1) return bad("mac must be 0 or 1");
+    if (p->mac == 1 && !(p->a_err > 0.0)) return bad("a_err must be > 0 for the absolute MAC");
+    return true;
+}
+
+SysParams make_sp(const hybrid_params &p)
+{
+    SysParams s;
+    memset(&s, 0, sizeof(s));
+    s.G = p.G;
+    s.eps2 = p.eps * p.eps;
+    s.theta = p.theta;
+    s.R1 = p.R1;
+    s.R2 = p.R2;
+    s.dt_soft = p.dt_soft;
+    s.a_err = p.a_err;
+    s.has_hard = p.R2 > 0.0 ? 1 : 0;
+    s.R2sq = s.has_hard ? p.R2 * p.R2 : 0.0;
+    s.invdR = s.has_hard ? 1.0 / (p.R2 - p.R1) : 0.0;
+    s.Gf = (float)p.G;
+    s.eps2f = (float)s.eps2;
+    s.R2f = (float)p.R2;
+    s.R2sqf = (float)s.R2sq;
+    s.R2sqlo = (float)(s.R2sq - (double)s.R2sqf);
+    s.invdRf = (float)s.invdR;
+    s.mac = p.mac;
+    return s;
+}
+
+hybrid_status cuda_fail(hybrid_ctx *c, cudaError_t e, const char *what)
+{
+    set_err(c, "%s: %s", what, cudaGetErrorString(e));
+    return HYBRID_ECUDA;
+}
+
+// Node-capacity dependent buffers.
+bool alloc_nodes(hybrid_ctx *c, int64_t cap)
+{
+    const size_t n = (size_t)cap;
+    bool ok = true;
+    for (Buf *b : {&c->nfirst, &c->ncount, &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->nchtmp})
+        ok = ok && ensure(c, *b, n * 4);
+    for (Buf *b : {&c->nM, &c->ncx, &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nrb, &c->nhr, &c->ndelta, &c->nside})
+        ok = ok && ensure(c, *b, n * 8);
+    ok = ok && ensure(c, c->norg, n * 24);
+    ok = ok && ensure(c, c->nA, n * 16) && ensure(c, c->nB, n * 16) && ensure(c, c->ncrit, n * 8);
+    ok = ok && ensure(c, c->ntopo, n * 16) && ensure(c, c->nD, n * 32);
+    if (ok) c->capNodes = cap;
+    return ok;
+}
+
+bool reserve(hybrid_ctx *c)
+{
+    const int64_t N = c->N, S = c->S;
+    bool ok = true;
+    if (N > c->capN) {
+        const size_t n = (size_t)N;
+        for (int f = 0; f < 7; ++f) ok = ok && ensure(c, c->x[f], n * 8) && ensure(c, c->xa[f], n * 8);
+        for (Buf *b : {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->leafof, &c->gflag, &c->gscan, &c->gnode,
+                       &c->gfirst, &c->gcount, &c->gsys})
+            ok = ok && ensure(c, *b, n * 4);
+        const size_t asz = c->p.precision == 1 ? 4 : 8;
+        for (int d = 0; d < 3; ++d) ok = ok && ensure(c, c->acc_s[d], n * asz) && ensure(c, c->acc_h[d], n * asz);
+        if (c->p.precision == 1) ok = ok && ensure(c, c->phi, n * 16) && ensure(c, c->plo, n * 16);
+        else ok = ok && ensure(c, c->pd, n * 32);
+        ok = ok && ensure(c, c->keys[0], n * 8) && ensure(c, c->keys[1], n * 8);
+        ok = ok && ensure(c, c->vals[0], n * 4) && ensure(c, c->vals[1], n * 4);
+        ok = ok && ensure(c, c->gF, n * sizeof(GroupF)) && ensure(c, c->glo, n * 24) && ensure(c, c->ghi, n * 24);
+        ok = ok && ensure(c, c->lcnt, (3 * n + 2) * 8);
+        if (ok) {
+            c->capN = N;
+            c->capGroups = N;
+        }
+    }
+    if (S > c->capS) {
+        const size_t s = (size_t)S;
+        ok = ok && ensure(c, c->off_dev, (s + 1) * 8) && ensure(c, c->sp_dev, s * sizeof(SysParams));
+        ok = ok && ensure(c, c->boxmin, s * 24) && ensure(c, c->boxmax, s * 24) && ensure(c, c->box, s * sizeof(SysBox));
+        ok = ok && ensure(c, c->sysroot, s * 4) && ensure(c, c->io_dev, s * sizeof(SysIO));
+        ok = ok && ensure(c, c->energy_dev, s * 16);
+        if (ok) c->capS = S;
+    }
+    if (c->nchunks > c->capChunks) {
+        ok = ok && ensure(c, c->chunks_dev, (size_t)c->nchunks * sizeof(Chunk)) &&
+             ensure(c, c->hist, (size_t)c->nchunks * 256 * 4);
+        if (ok) c->capChunks = c->nchunks;
+    }
+    if (c->capNodes < std::max<int64_t>(4096, N)) ok = ok && alloc_nodes(c, std::max<int64_t>(4096, N));
+    if (c->capList < std::max<int64_t>(1 << 20, 128 * N)) {
+        ok = ok && ensure(c, c->list, (size_t)std::max<int64_t>(1 << 20, 128 * N) * 4);
+        if (ok) c->capList = std::max<int64_t>(1 << 20, 128 * N);
+    }
+    if (c->capStack == 0) c->capStack = 4096;
+    ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * c->capStack * 4);
+    // scratch of the scans: the longest scan is over max(N, nodes, 3 groups + 1, tiles x 256)
+    const int64_t longest = std::max<int64_t>({N, c->capNodes, 3 * c->capGroups + 2, (int64_t)c->nchunks * 256});
+    ok = ok && ensure(c, c->blocksum, (size_t)((longest + SCAN_SEG - 1) / SCAN_SEG + 1) * 8);
+    return ok;
+}
+
+// Validates the systems, lays them out back to back, builds the radix tiles
+// and the per-system parameter table, and reserves every buffer.
+hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool need_acc)
+{
+    if (!sys || S < 1) {
+        set_err(c, "no systems");
+        return HYBRID_EINVAL;
+    }
+    c->h_off.assign(S + 1, 0);
+    c->h_sp.resize(S);
+    for (int s = 0; s < S; ++s) {
+        const hybrid_system &y = sys[s];
+        if (y.n < 1) {
+            set_err(c, "system %d: n must be >= 1", s);
+            return HYBRID_EINVAL;
+        }
+        if (!y.x || !y.y || !y.z || !y.vx || !y.vy || !y.vz || !y.m) {
+            set_err(c, "system %d: null state pointer", s);
+            return HYBRID_EINVAL;
+        }
+        if (need_acc && (!y.ax_s || !y.ay_s || !y.az_s || !y.ax_h || !y.ay_h || !y.az_h)) {
+            set_err(c, "system %d: null acceleration pointer", s);
+            return HYBRID_EINVAL;
+        }
+        hybrid_params p = c->p;
+        if (y.params) {
+            const hybrid_params &q = *y.params;
+            p.G = q.G;
+            p.eps = q.eps;
+            p.theta = q.theta;
+            p.R1 = q.R1;
+            p.R2 = q.R2;
+            p.dt_soft = q.dt_soft;
+            p.a_err = q.a_err;
+            p.mac = q.mac;
+            std::string why;
+            if (!params_ok(&p, &why)) {
+                set_err(c, "system %d: %s", s, why.c_str());
+                return HYBRID_EINVAL;
+            }
+        }
+        c->h_sp[s] = make_sp(p);
+        c->h_off[s + 1] = c->h_off[s] + y.n;
+    }
+    if (c->h_off[S] >= (int64_t)0x7fffffff) {
+        set_err(c, "too many particles (%lld)", (long long)c->h_off[S]);
+        return HYBRID_EINVAL;
+    }
+    c->S = S;
+    c->N = c->h_off[S];
+    c->h_chunks.clear();
+    for (int s = 0; s < S; ++s) {
+        const int first = (int)c->h_chunks.size();
+        const int64_t n = c->h_off[s + 1] - c->h_off[s];
+        const int nch = (int)((n + RS_TILE - 1) / RS_TILE);
+        for (int k = 0; k < nch; ++k) {
+            Chunk ch;
+            ch.start = c->h_off[s] + (int64_t)k * RS_TILE;
+            ch.len = (int)std::min<int64_t>(RS_TILE, n - (int64_t)k * RS_TILE);
+            ch.sys = s;
+            ch.first_chunk = first;
+            ch.nchunk = nch;
+            c->h_chunks.push_back(ch);
+        }
+    }
+    c->nchunks = (int)c->h_chunks.size();
+    if (!reserve(c)) return HYBRID_ENOMEM;
+    c->h_io.resize(S);
+    for (int s = 0; s < S; ++s) {
+        const hybrid_system &y = sys[s];
+        SysIO &o = c->h_io[s];
+        o.x[0] = y.x;
+        o.x[1] = y.y;
+        o.x[2] = y.z;
+        o.x[3] = y.vx;
+        o.x[4] = y.vy;
+        o.x[5] = y.vz;
+        o.x[6] = y.m;
+        o.id = y.id;
+        o.as[0] = y.ax_s;
+        o.as[1] = y.ay_s;
+        o.as[2] = y.az_s;
+        o.ah[0] = y.ax_h;
+        o.ah[1] = y.ay_h;
+        o.ah[2] = y.az_h;
+        o.n = y.n;
+        o.off = c->h_off[s];
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->off_dev.p, c->h_off.data(), (S + 1) * 8, cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(c->sp_dev.p, c->h_sp.data(), S * sizeof(SysParams), cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(c->chunks_dev.p, c->h_chunks.data(), c->nchunks * sizeof(Chunk),
+                             cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(c->io_dev.p, c->h_io.data(), S * sizeof(SysIO), cudaMemcpyHostToDevice, c->st)))
+        return cuda_fail(c, e, "upload of the batch tables");
+    c->tree_valid = false;
+    return HYBRID_OK;
+}
+
+// ---- ops ----
+enum OpKind { OP_KICKS, OP_BUILD, OP_WALK, OP_PAIR_H, OP_PAIR_S };
+struct Op {
+    int kind = OP_BUILD;
+    int mode = 0;
+    int nk = 0;
+    int which[4] = {0, 0, 0, 0};
+    int kmode[4] = {0, 0, 0, 0};
+    double val[4] = {0, 0, 0, 0};
+    int dmode = -1;
+    double dval = 0.0;
+};
+
+void enqueue(hybrid_ctx *c, const Op &o, int idx)
+{
+    c->op = idx;
+    switch (o.kind) {
+    case OP_KICKS:
+        launch_kick_seq(c, o.nk, o.which, o.kmode, o.val, o.dmode, o.dval);
+        break;
+    case OP_BUILD: {
+        cudaEvent_t e0 = nullptr;
+        prof_begin(c, PROF_TREE, &e0);
+        launch_box(c);
+        launch_keys_sort_permute(c);
+        launch_build_levels(c);
+        launch_moments(c);
+        launch_groups(c);
+        prof_end(c, PROF_TREE, e0);
+        break;
+    }
+    case OP_WALK:
+        launch_walk(c, o.mode);
+        break;
+    case OP_PAIR_H:
+        launch_pair_hard(c);
+        break;
+    case OP_PAIR_S:
+        launch_pair_soft(c);
+        break;
+    }
+}
+
+hybrid_status read_status(hybrid_ctx *c, Status *out)
+{
+    cudaError_t e = cudaMemcpyAsync(c->h_status, c->status.p, sizeof(Status), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronisation");
+    *out = *c->h_status;
+    return HYBRID_OK;
+}
+
+hybrid_status clear_status(hybrid_ctx *c)
+{
+    cudaError_t e = cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->st);
+    return e == cudaSuccess ? HYBRID_OK : cuda_fail(c, e, "status reset");
+}
+
+hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
+{
+    size_t start = 0;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        for (size_t i = start; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
+        cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess) return cuda_fail(c, le, "kernel launch");
+        Status s;
+        hybrid_status r = read_status(c, &s);
+        if (r != HYBRID_OK) return r;
+        if (s.code == 0) return HYBRID_OK;
+        if (s.code != HYBRID_ECAPACITY) {
+            set_err(c, "device failure %d at op %d", s.code, s.where);
+            clear_status(c);
+            return (hybrid_status)s.code;
+        }
+        // grow what overflowed, then resume at the build of the failed evaluation
+        bool ok = true;
+        if (s.need[0] > c->capNodes) ok = ok && alloc_nodes(c, s.need[0]);
+        if (s.need[1] > c->capList) {
+            const int64_t cap = s.need[1] + s.need[1] / 4 + 1024;
+            ok = ok && ensure(c, c->list, (size_t)cap * 4);
+            if (ok) c->capList = cap;
+        }
+        if (s.need[2] > c->capStack) {
+            ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * s.need[2] * 4);
+            if (ok) c->capStack = s.need[2];
+        }
+        const int64_t longest = std::max<int64_t>({c->N, c->capNodes, 3 * c->capGroups + 2, (int64_t)c->nchunks * 256});
+        ok = ok && ensure(c, c->blocksum, (size_t)((longest + SCAN_SEG - 1) / SCAN_SEG + 1) * 8);
+        if (!ok) return HYBRID_ENOMEM;
+        if ((r = clear_status(c)) != HYBRID_OK) return r;
+        start = (size_t)std::max(0, s.where);
+        while (start > 0 && ops[start].kind != OP_BUILD) --start;
+    }
+    set_err(c, "capacity could not be grown enough");
+    return HYBRID_ECAPACITY;
+}
+
+Op kicks(int nk, const int *which, const int *kmode, int dmode)
+{
+    Op o;
+    o.kind = OP_KICKS;
+    o.nk = nk;
+    for (int k = 0; k < nk; ++k) {
+        o.which[k] = which[k];
+        o.kmode[k] = kmode[k];
+    }
+    o.dmode = dmode;
+    return o;
+}
+
+Op simple(int kind, int mode = 0)
+{
+    Op o;
+    o.kind = kind;
+    o.mode = mode;
+    return o;
+}
+
+// The op sequence of n_steps soft steps (Sec. II-C, kick-drift-kick):
+// K_s(dt_s/2); n x [K_h(dt_h/2); D(dt_h); build; hard (+ soft at the last);
+// K_h(dt_h/2)]; K_s(dt_s/2). Adjacent kicks share one launch (same order).
+std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid)
+{
+    std::vector<Op> ops;
+    if (!valid) {
+        ops.push_back(simple(OP_BUILD));
+        ops.push_back(simple(OP_WALK, 3));
+        ops.push_back(simple(OP_PAIR_H));
+        ops.push_back(simple(OP_PAIR_S));
+    }
+    int pw[8], pm[8], np = 0;
+    auto add = [&](int which, int mode) {
+        pw[np] = which;
+        pm[np] = mode;
+        ++np;
+    };
+    const int nh = c->p.n_hard;
+    for (int s = 0; s < n_steps; ++s) {
+        add(0, 1);
+        for (int k = 1; k <= nh; ++k) {
+            add(1, 2);
+            ops.push_back(kicks(np, pw, pm, 2));
+            np = 0;
+            ops.push_back(simple(OP_BUILD));
+            ops.push_back(simple(OP_WALK, k == nh ? 3 : 2));
+            ops.push_back(simple(OP_PAIR_H));
+            if (k == nh) ops.push_back(simple(OP_PAIR_S));
+            add(1, 2);
+        }
+        add(0, 1);
+    }
+    if (np) ops.push_back(kicks(np, pw, pm, -1));
+    return ops;
+}
+
+hybrid_status finish(hybrid_ctx *c, hybrid_status r)
+{
+    if (r == HYBRID_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    }
+    return r;
+}
+
+template <typename T>
+bool d2h(hybrid_ctx *c, std::vector<T> &v, const Buf &b, size_t n)
+{
+    v.resize(n);
+    if (n == 0) return true;
+    return cudaMemcpyAsync(v.data(), b.p, n * sizeof(T), cudaMemcpyDeviceToHost, c->st) == cudaSuccess;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stream)
+{
+    if (!out || !p) return HYBRID_EINVAL;
+    *out = nullptr;
+    if (!params_ok(p, nullptr)) return HYBRID_EINVAL;
+    hybrid_ctx *c = new hybrid_ctx();
+    c->p = *p;
+    c->st = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e != cudaSuccess) {
+        delete c;
+        return HYBRID_ECUDA;
+    }
+    c->walk_warps = c->nsm * 16;
+    bool ok = ensure(c, c->status, sizeof(Status)) && ensure(c, c->counter, 16 * 8) && ensure(c, c->lvl, 1024) &&
+              ensure(c, c->ngroups_dev, 64);
+    if (!ok) {
+        hybrid_destroy(c);
+        return HYBRID_ENOMEM;
+    }
+    if (cudaMallocHost((void **)&c->h_status, sizeof(Status)) != cudaSuccess) {
+        hybrid_destroy(c);
+        return HYBRID_ENOMEM;
+    }
+    cudaMemsetAsync(c->status.p, 0, sizeof(Status), c->st);
+    cudaMemsetAsync(c->counter.p, 0, 16 * 8, c->st);
+    cudaMemsetAsync(c->ngroups_dev.p, 0, 64, c->st);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) {
+        hybrid_destroy(c);
+        return HYBRID_ECUDA;
+    }
+    *out = c;
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_destroy(hybrid_ctx *c)
+{
+    if (!c) return HYBRID_OK;
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    Buf *all[] = {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->phi, &c->plo, &c->pd, &c->keys[0], &c->keys[1],
+                  &c->vals[0], &c->vals[1], &c->hist, &c->blocksum, &c->off_dev, &c->sp_dev, &c->chunks_dev,
+                  &c->boxmin, &c->boxmax, &c->box, &c->sysroot, &c->status, &c->lvl, &c->nfirst, &c->ncount,
+                  &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->nchtmp, &c->leafof, &c->nM, &c->ncx,
+                  &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
+                  &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
+                  &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,
+                  &c->io_dev, &c->energy_dev};
+    for (Buf *b : all)
+        if (b->p) cudaFree(b->p);
+    for (int f = 0; f < 7; ++f) {
+        if (c->x[f].p) cudaFree(c->x[f].p);
+        if (c->xa[f].p) cudaFree(c->xa[f].p);
+    }
+    for (int d = 0; d < 3; ++d) {
+        if (c->acc_s[d].p) cudaFree(c->acc_s[d].p);
+        if (c->acc_h[d].p) cudaFree(c->acc_h[d].p);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (auto &u : c->ev_used) {
+        cudaEventDestroy(u.second.first);
+        cudaEventDestroy(u.second.second);
+    }
+    if (c->h_status) cudaFreeHost(c->h_status);
+    delete c;
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_build_tree(hybrid_ctx *c, hybrid_system *sys)
+{
+    if (!c || !sys) return HYBRID_EINVAL;
+    hybrid_status r = setup_batch(c, sys, 1, false);
+    if (r != HYBRID_OK) return r;
+    launch_copy_in(c, (const SysIO *)c->io_dev.p, false);
+    r = run_ops(c, {simple(OP_BUILD)});
+    if (r != HYBRID_OK) return r;
+    launch_copy_out(c, (const SysIO *)c->io_dev.p, true, false, false);
+    sys->forces_valid = 0;
+    c->tree_valid = true;
+    c->have_soft = c->have_hard = false;
+    return finish(c, HYBRID_OK);
+}
+
+hybrid_status force_call(hybrid_ctx *c, hybrid_system *sys, bool soft)
+{
+    if (!c || !sys) return HYBRID_EINVAL;
+    if (!c->tree_valid || c->S != 1 || c->N != sys->n) {
+        set_err(c, "no tree for this system: call hybrid_build_tree first");
+        return HYBRID_EINVAL;
+    }
+    void *a[3] = {soft ? sys->ax_s : sys->ax_h, soft ? sys->ay_s : sys->ay_h, soft ? sys->az_s : sys->az_h};
+    if (!a[0] || !a[1] || !a[2]) {
+        set_err(c, "null acceleration pointer");
+        return HYBRID_EINVAL;
+    }
+    // the output arrays may differ from the ones of the build call
+    SysIO &o = c->h_io[0];
+    for (int d = 0; d < 3; ++d) (soft ? o.as : o.ah)[d] = a[d];
+    cudaError_t e = cudaMemcpyAsync(c->io_dev.p, &o, sizeof(SysIO), cudaMemcpyHostToDevice, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    hybrid_status r = run_ops(c, {simple(OP_WALK, soft ? 1 : 2), simple(soft ? OP_PAIR_S : OP_PAIR_H)});
+    if (r != HYBRID_OK) return r;
+    launch_copy_out(c, (const SysIO *)c->io_dev.p, false, soft, !soft);
+    (soft ? c->have_soft : c->have_hard) = true;
+    sys->forces_valid = (c->have_soft && c->have_hard) ? 1 : 0;
+    return finish(c, HYBRID_OK);
+}
+
+hybrid_status hybrid_soft_force(hybrid_ctx *c, hybrid_system *sys) { return force_call(c, sys, true); }
+hybrid_status hybrid_hard_force(hybrid_ctx *c, hybrid_system *sys) { return force_call(c, sys, false); }
+
+hybrid_status hybrid_kick(hybrid_ctx *c, hybrid_system *sys, int which, double dt)
+{
+    if (!c || !sys || (which != 0 && which != 1) || sys->n < 1 || !sys->vx || !sys->vy || !sys->vz) return HYBRID_EINVAL;
+    if (which == 0 && (!sys->ax_s || !sys->ay_s || !sys->az_s)) return HYBRID_EINVAL;
+    if (which == 1 && (!sys->ax_h || !sys->ay_h || !sys->az_h)) return HYBRID_EINVAL;
+    launch_kick_ext(c, sys, which, dt);
+    return finish(c, HYBRID_OK);
+}
+
+hybrid_status hybrid_drift(hybrid_ctx *c, hybrid_system *sys, double dt)
+{
+    if (!c || !sys || sys->n < 1 || !sys->x || !sys->y || !sys->z || !sys->vx || !sys->vy || !sys->vz)
+        return HYBRID_EINVAL;
+    launch_drift_ext(c, sys, dt);
+    sys->forces_valid = 0;
+    return finish(c, HYBRID_OK);
+}
+
+hybrid_status hybrid_step_batched(hybrid_ctx *c, hybrid_system *sys, int n_sys, int n_soft_steps)
+{
+    if (!c || !sys || n_sys < 1 || n_soft_steps < 0) return HYBRID_EINVAL;
+    hybrid_status r = setup_batch(c, sys, n_sys, true);
+    if (r != HYBRID_OK) return r;
+    bool valid = true;
+    for (int s = 0; s < n_sys; ++s) valid = valid && sys[s].forces_valid;
+    launch_copy_in(c, (const SysIO *)c->io_dev.p, valid);
+    r = run_ops(c, step_ops(c, n_soft_steps, valid));
+    if (r != HYBRID_OK) return r;
+    launch_copy_out(c, (const SysIO *)c->io_dev.p, true, true, true);
+    Status s;
+    if ((r = read_status(c, &s)) != HYBRID_OK) return r;
+    for (int k = 0; k < n_sys; ++k) sys[k].forces_valid = 1;
+    c->tree_valid = (n_sys == 1);
+    c->have_soft = c->have_hard = true;
+    return finish(c, HYBRID_OK);
+}
+
+hybrid_status hybrid_step(hybrid_ctx *c, hybrid_system *sys, int n_soft_steps)
+{
+    return hybrid_step_batched(c, sys, 1, n_soft_steps);
+}
+
+hybrid_status hybrid_get_perm(hybrid_ctx *c, int32_t *dev_perm)
+{
+    if (!c || !dev_perm || c->N == 0) return HYBRID_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(dev_perm, c->orig.p, (size_t)c->N * 4, cudaMemcpyDeviceToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    return e == cudaSuccess ? HYBRID_OK : cuda_fail(c, e, "perm copy");
+}
+
+hybrid_status hybrid_sync(hybrid_ctx *c)
+{
+    if (!c) return HYBRID_EINVAL;
+    Status s;
+    hybrid_status r = read_status(c, &s);
+    if (r != HYBRID_OK) return r;
+    if (s.code) {
+        set_err(c, "device failure %d at op %d", s.code, s.where);
+        clear_status(c);
+        return (hybrid_status)s.code;
+    }
+    return HYBRID_OK;
+}
+
+const char *hybrid_last_error(hybrid_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+hybrid_status hybrid_tree_info(hybrid_ctx *c, int64_t *n_nodes, int64_t *n_groups)
+{
+    if (!c || !c->tree_valid) return HYBRID_EINVAL;
+    uint32_t lv[LEVELS + 3];
+    int64_t ng = 0;
+    cudaError_t e = cudaMemcpyAsync(lv, c->lvl.p, sizeof(lv), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ng, c->ngroups_dev.p, 8, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tree info");
+    if (n_nodes) *n_nodes = lv[LEVELS + 1];
+    if (n_groups) *n_groups = ng;
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_tree_copy(hybrid_ctx *c, uint64_t *keys, int32_t *level, int64_t *first, int64_t *count,
+                               int64_t *child, int32_t *nchild, int64_t *parent, double *moments, int64_t *group_node,
+                               double *group_lo, double *group_hi)
+{
+    int64_t nn = 0, ng = 0;
+    hybrid_status r = hybrid_tree_info(c, &nn, &ng);
+    if (r != HYBRID_OK) return r;
+    std::vector<uint32_t> f, cn, ch, nc, pa, lv, gn;
+    std::vector<double> M, cx, cy, cz, bm, B2, de, sd, og, rb, glo, ghi;
+    std::vector<uint64_t> k;
+    bool ok = d2h(c, f, c->nfirst, nn) && d2h(c, cn, c->ncount, nn) && d2h(c, ch, c->nchild, nn) &&
+              d2h(c, nc, c->nnch, nn) && d2h(c, pa, c->nparent, nn) && d2h(c, lv, c->nlevel, nn) &&
+              d2h(c, gn, c->gnode, ng) && d2h(c, M, c->nM, nn) && d2h(c, cx, c->ncx, nn) && d2h(c, cy, c->ncy, nn) &&
+              d2h(c, cz, c->ncz, nn) && d2h(c, bm, c->nbmax, nn) && d2h(c, B2, c->nB2, nn) &&
+              d2h(c, de, c->ndelta, nn) && d2h(c, sd, c->nside, nn) && d2h(c, og, c->norg, 3 * nn) &&
+              d2h(c, rb, c->nrb, nn) && d2h(c, glo, c->glo, 3 * ng) && d2h(c, ghi, c->ghi, 3 * ng) &&
+              d2h(c, k, c->keys[0], c->N);
+    if (!ok || cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "tree copy");
+    for (int64_t i = 0; i < nn; ++i) {
+        if (level) level[i] = (int32_t)lv[i];
+        if (first) first[i] = f[i];
+        if (count) count[i] = cn[i];
+        if (child) child[i] = nc[i] ? (int64_t)ch[i] : -1;
+        if (nchild) nchild[i] = (int32_t)nc[i];
+        if (parent) parent[i] = pa[i] == NONE ? -1 : (int64_t)pa[i];
+        if (moments) {
+            double *o = moments + 13 * i;
+            o[0] = M[i];
+            o[1] = cx[i];
+            o[2] = cy[i];
+            o[3] = cz[i];
+            o[4] = bm[i];
+            o[5] = B2[i];
+            o[6] = de[i];
+            o[7] = sd[i];
+            o[8] = og[3 * i];
+            o[9] = og[3 * i + 1];
+            o[10] = og[3 * i + 2];
+            o[11] = rb[i];
+            o[12] = 0.0;
+        }
+    }
+    for (int64_t g = 0; g < ng; ++g) {
+        if (group_node) group_node[g] = gn[g];
+        for (int d = 0; d < 3; ++d) {
+            if (group_lo) group_lo[3 * g + d] = glo[3 * g + d];
+            if (group_hi) group_hi[3 * g + d] = ghi[3 * g + d];
+        }
+    }
+    if (keys) memcpy(keys, k.data(), (size_t)c->N * 8);
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_lists_copy(hybrid_ctx *c, int64_t *counts, int64_t *entries, int64_t cap_entries)
+{
+    int64_t nn = 0, ng = 0;
+    hybrid_status r = hybrid_tree_info(c, &nn, &ng);
+    if (r != HYBRID_OK) return r;
+    std::vector<uint64_t> off;
+    if (!d2h(c, off, c->lcnt, 3 * ng + 1) || cudaStreamSynchronize(c->st) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "list copy");
+    const uint64_t total = off[3 * ng];
+    for (int64_t g = 0; g < ng; ++g)
+        for (int k = 0; k < 3; ++k) counts[3 * g + k] = (int64_t)(off[k * ng + g + 1] - off[k * ng + g]);
+    if (!entries) return HYBRID_OK;
+    if ((int64_t)total > cap_entries) return HYBRID_EINVAL;
+    std::vector<uint32_t> L;
+    if (!d2h(c, L, c->list, total) || cudaStreamSynchronize(c->st) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "list copy");
+    int64_t o = 0;
+    for (int64_t g = 0; g < ng; ++g)
+        for (int k = 0; k < 3; ++k)
+            for (uint64_t j = off[k * ng + g]; j < off[k * ng + g + 1]; ++j) entries[o++] = L[j];
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_interactions(hybrid_ctx *c, int64_t *soft, int64_t *hard)
+{
+    if (!c) return HYBRID_EINVAL;
+    uint64_t v[16];
+    cudaError_t e = cudaMemcpyAsync(v, c->counter.p, sizeof(v), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "counters");
+    if (soft) *soft = (int64_t)v[6];
+    if (hard) *hard = (int64_t)v[7];
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_profile(hybrid_ctx *c, int enable)
+{
+    if (!c) return HYBRID_EINVAL;
+    c->prof = enable != 0;
+    return HYBRID_OK;
+}
+
+hybrid_status hybrid_profile_read(hybrid_ctx *c, int kind, double *ms, int64_t *launches, int reset)
+{
+    if (!c || kind < 0 || kind >= PROF_KINDS) return HYBRID_EINVAL;
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "profile sync");
+    for (auto &u : c->ev_used) {
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, u.second.first, u.second.second);
+        c->prof_ms[u.first] += t;
+        c->prof_n[u.first] += 1;
+        c->ev_pool.push_back(u.second.first);
+        c->ev_pool.push_back(u.second.second);
+    }
+    c->ev_used.clear();
+    if (ms) *ms = c->prof_ms[kind];
+    if (launches) *launches = c->prof_n[kind];
+    if (reset)
+        for (int k = 0; k < PROF_KINDS; ++k) {
+            c->prof_ms[k] = 0.0;
+            c->prof_n[k] = 0;
+        }
+    return HYBRID_OK;
+}
+
+int64_t hybrid_launch_count(hybrid_ctx *c) { return c ? c->launches : 0; }
+
+hybrid_status hybrid_energy(hybrid_ctx *c, hybrid_system *sys, double *kinetic, double *potential)
+{
+    if (!c || !sys || !kinetic || !potential) return HYBRID_EINVAL;
+    hybrid_status r = setup_batch(c, sys, 1, false);
+    if (r != HYBRID_OK) return r;
+    launch_copy_in(c, (const SysIO *)c->io_dev.p, false);
+    launch_energy(c, (double *)c->energy_dev.p);
+    double v[2];
+    cudaError_t e = cudaMemcpyAsync(v, c->energy_dev.p, 16, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "energy");
+    *kinetic = v[0];
+    *potential = v[1];
+    return HYBRID_OK;
+}
+
+}  // extern "C"

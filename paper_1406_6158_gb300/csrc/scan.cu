@@ -1,0 +1,157 @@
+// scan.cu -- exclusive prefix sums whose length may live on the device.
+//
+// Three launches: per-segment sums, one-block scan of the segment sums, and a
+// per-segment block scan that adds the segment offset. The length is read
+// from device memory when the caller has no host copy (tree levels, group
+// counts), so the sequence never waits on the host.
+#include "hy_internal.cuh"
+
+namespace hy {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+}  // namespace
+
+// Block-wide exclusive scan of one value per thread; every thread also gets
+// the block total.
+template <typename T>
+__device__ __forceinline__ T block_scan_with_total(T v, T &total)
+{
+    __shared__ T wsum[SCAN_THREADS / 32];
+    __shared__ T tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        T s = (lane < SCAN_THREADS / 32) ? wsum[lane] : T(0);
+        T si = warp_incl_scan(s);
+        if (lane < SCAN_THREADS / 32) wsum[lane] = si - s;
+        if (lane == SCAN_THREADS / 32 - 1) tot = si;
+    }
+    __syncthreads();
+    T r = wsum[w] + inc - v;
+    total = tot;
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T *data, int64_t n_host, const int64_t *d_n,
+                                                               uint64_t *bsum, const Status *st)
+{
+    if (st->code) return;
+    const int64_t n = d_n ? *d_n : n_host;
+    const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
+    for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const int64_t base = s * SCAN_SEG + (int64_t)threadIdx.x * SCAN_IPT;
+        uint64_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_IPT; ++k)
+            if (base + k < n) acc += (uint64_t)data[base + k];
+        uint64_t tot;
+        block_scan_with_total<uint64_t>(acc, tot);
+        if (threadIdx.x == 0) bsum[s] = tot;
+    }
+}
+
+// One block: exclusive scan of the segment sums; writes the grand total.
+__global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *bsum, int64_t n_host, const int64_t *d_n,
+                                                     uint64_t *d_total, const Status *st)
+{
+    if (st->code) return;
+    const int64_t n = d_n ? *d_n : n_host;
+    const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < nseg; b0 += 1024) {
+        const int64_t i = b0 + threadIdx.x;
+        uint64_t v = (i < nseg) ? bsum[i] : 0;
+        uint64_t inc = warp_incl_scan(v);
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            uint64_t s = wsum[lane];
+            uint64_t si = warp_incl_scan(s);
+            wsum[lane] = si - s;
+        }
+        __syncthreads();
+        const uint64_t c0 = carry;
+        if (i < nseg) bsum[i] = c0 + wsum[w] + inc - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c0 + wsum[w] + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(T *data, int64_t n_host, const int64_t *d_n,
+                                                             const uint64_t *bsum, const Status *st)
+{
+    if (st->code) return;
+    const int64_t n = d_n ? *d_n : n_host;
+    const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
+    for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
+        const int64_t base = s * SCAN_SEG + (int64_t)threadIdx.x * SCAN_IPT;
+        T v[SCAN_IPT];
+        uint64_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < SCAN_IPT; ++k) {
+            v[k] = (base + k < n) ? data[base + k] : T(0);
+            acc += (uint64_t)v[k];
+        }
+        uint64_t tot;
+        uint64_t ex = block_scan_with_total<uint64_t>(acc, tot) + bsum[s];
+#pragma unroll
+        for (int k = 0; k < SCAN_IPT; ++k) {
+            if (base + k < n) data[base + k] = (T)ex;
+            ex += (uint64_t)v[k];
+        }
+    }
+}
+
+template <typename T>
+static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+{
+    const int64_t nseg_max = (n_max + SCAN_SEG - 1) / SCAN_SEG;
+    if (nseg_max <= 0) {
+        if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c->st);
+        return;
+    }
+    ensure(c, c->blocksum, (size_t)nseg_max * sizeof(uint64_t));
+    uint64_t *bs = (uint64_t *)c->blocksum.p;
+    const int grid = (int)std::min<int64_t>(nseg_max, (int64_t)c->nsm * 8);
+    Status *st = status_dev(c);
+    k_scan_reduce<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
+    k_scan_spine<<<1, 1024, 0, c->st>>>(bs, n_host, d_n, d_total, st);
+    k_scan_down<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
+    c->launches += 3;
+}
+
+void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+{
+    scan_impl<uint32_t>(c, data, n_host, d_n, n_max, d_total);
+}
+
+void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+{
+    scan_impl<uint64_t>(c, data, n_host, d_n, n_max, d_total);
+}
+
+}  // namespace hy

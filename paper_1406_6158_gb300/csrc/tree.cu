@@ -1,0 +1,953 @@
+// tree.cu -- octree construction on the device (Sec. III-A1 of the paper,
+// done on the GPU instead of the host): root cube, Morton keys, a stable LSD
+// radix sort of the keys with the particle data gathered into key order, a
+// level-wise split (a cell with more than n_leaf particles splits into its
+// non-empty octants), cell moments (Sec. II-B: mass, centre of mass; Eq. 5-6:
+// b_max, B2, MAC radius) and the sink groups.
+//
+// All systems of a batch are processed by the same launches; every node,
+// particle range and radix tile stays inside one system.
+#include "hy_internal.cuh"
+
+#include <cstdio>
+
+namespace hy {
+
+namespace {
+
+__device__ __forceinline__ void fail(Status *st, int code, int where)
+{
+    atomicCAS(&st->code, 0, code);
+    st->where = where;
+}
+
+// order-preserving map of doubles to unsigned integers (for atomic min/max)
+__device__ __forceinline__ unsigned long long ord_dbl(double v)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord_dbl(unsigned long long u)
+{
+    return __longlong_as_double((long long)((u >> 63) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
+// ---------------------------------------------------------------------------
+// Root cube: per-axis minimum lo; side L = smallest power of two >= the
+// largest extent (1 when all particles coincide); scale = 2^21 / L.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_box(const double *__restrict__ x, const double *__restrict__ y,
+                                             const double *__restrict__ z, const Chunk *__restrict__ chunks,
+                                             int nchunks, unsigned long long *bmin, unsigned long long *bmax,
+                                             const Status *st)
+{
+    if (st->code) return;
+    __shared__ double sh[6][8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunks[c];
+        double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (int i = threadIdx.x; i < ch.len; i += blockDim.x) {
+            const int64_t k = ch.start + i;
+            const double p0 = x[k], p1 = y[k], p2 = z[k];
+            v[0] = fmin(v[0], p0);
+            v[1] = fmin(v[1], p1);
+            v[2] = fmin(v[2], p2);
+            v[3] = fmax(v[3], p0);
+            v[4] = fmax(v[4], p1);
+            v[5] = fmax(v[5], p2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = fmin(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+#pragma unroll
+            for (int j = 3; j < 6; ++j) v[j] = fmax(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+        }
+        if (lane == 0)
+            for (int j = 0; j < 6; ++j) sh[j][w] = v[j];
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            const int j = threadIdx.x;
+            double r = sh[j][0];
+            for (int k = 1; k < 8; ++k) r = (j < 3) ? fmin(r, sh[j][k]) : fmax(r, sh[j][k]);
+            if (j < 3) atomicMin(&bmin[3 * ch.sys + j], ord_dbl(r));
+            else atomicMax(&bmax[3 * ch.sys + j - 3], ord_dbl(r));
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_box_final(int S, const unsigned long long *bmin, const unsigned long long *bmax, SysBox *box,
+                            const Status *st)
+{
+    if (st->code) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    double lo[3], ext = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = unord_dbl(bmin[3 * s + d]);
+        const double e = __dsub_rn(unord_dbl(bmax[3 * s + d]), lo[d]);
+        if (e > ext) ext = e;
+    }
+    double L = 1.0;
+    if (ext > 0.0) {
+        int e2;
+        const double f = frexp(ext, &e2);
+        L = (f == 0.5) ? ext : ldexp(1.0, e2);
+    }
+    SysBox b;
+    b.lo[0] = lo[0];
+    b.lo[1] = lo[1];
+    b.lo[2] = lo[2];
+    b.L = L;
+    b.scale = ldexp(1.0, LEVELS) / L;   // ratio of powers of two: exact
+    b.u = ldexp(L, -20);
+    b.inv_u = ldexp(1.0, 20) / L;
+    b.pad = 0.0;
+    box[s] = b;
+}
+
+// ---------------------------------------------------------------------------
+// Morton keys: q = clamp(floor((x - lo) * scale), 0, 2^21 - 1) per axis, bits
+// interleaved from the top, x first. Only the subtraction rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x1f00000000ffffull;
+    x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t cell_coord(double p, double lo, double scale)
+{
+    double t = floor(__dmul_rn(__dsub_rn(p, lo), scale));
+    t = t < 0.0 ? 0.0 : t;
+    t = t > (double)((1u << LEVELS) - 1u) ? (double)((1u << LEVELS) - 1u) : t;
+    return (uint32_t)t;
+}
+
+// FP32 hi/lo copy of a coordinate relative to the root corner: hi = the
+// nearest multiple of u (at most 2^20 steps: exact in FP32), lo = the rest
+// (exact in FP64, then rounded to FP32, |lo| <= u/2).
+__device__ __forceinline__ void grid_split(double x, double lo0, const SysBox &b, float &h, float &l)
+{
+    const double xp = __dsub_rn(x, lo0);
+    const double hh = __dmul_rn(rint(__dmul_rn(xp, b.inv_u)), b.u);
+    h = (float)hh;
+    l = (float)__dsub_rn(xp, hh);
+}
+
+__global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restrict__ x, const double *__restrict__ y,
+                                              const double *__restrict__ z, const int32_t *__restrict__ psys,
+                                              const SysBox *__restrict__ box, uint64_t *__restrict__ key,
+                                              uint32_t *__restrict__ val, const Status *st)
+{
+    if (st->code) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const SysBox b = box[psys[i]];
+        const uint32_t qx = cell_coord(x[i], b.lo[0], b.scale);
+        const uint32_t qy = cell_coord(y[i], b.lo[1], b.scale);
+        const uint32_t qz = cell_coord(z[i], b.lo[2], b.scale);
+        key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        val[i] = (uint32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Stable LSD radix sort, 8-bit digits, tiles of RS_TILE keys inside one
+// system. The histogram of tile c for digit d goes to slot
+//   256 * first_chunk(s) + d * nchunk(s) + (c - first_chunk(s)),
+// so one flat exclusive scan yields, for every (tile, digit), the start of
+// its run inside its own system's segment.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t hist_slot(const Chunk &ch, int c, uint32_t d)
+{
+    return 256u * (uint32_t)ch.first_chunk + d * (uint32_t)ch.nchunk + (uint32_t)(c - ch.first_chunk);
+}
+
+__global__ void __launch_bounds__(256) k_radix_hist(const uint64_t *__restrict__ key, const Chunk *__restrict__ chunks,
+                                                    int nchunks, int shift, uint32_t *__restrict__ hist,
+                                                    const Status *st)
+{
+    if (st->code) return;
+    __shared__ uint32_t h[256];
+    const int lane = threadIdx.x & 31;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunks[c];
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        for (int i0 = 0; i0 < ch.len; i0 += blockDim.x) {
+            const int i = i0 + threadIdx.x;
+            const bool ok = i < ch.len;
+            const uint32_t d = ok ? (uint32_t)(key[ch.start + i] >> shift) & 0xffu : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            if (ok && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        hist[hist_slot(ch, c, threadIdx.x)] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restrict__ kin,
+                                                       const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+                                                       uint32_t *__restrict__ vout,
+                                                       const Chunk *__restrict__ chunks, int nchunks, int shift,
+                                                       const uint32_t *__restrict__ offs, const Status *st)
+{
+    if (st->code) return;
+    __shared__ uint32_t whist[RS_WARPS][256];
+    __shared__ uint32_t base[256];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned ltmask = (1u << lane) - 1u;
+    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const Chunk ch = chunks[c];
+        for (int t = threadIdx.x; t < RS_WARPS * 256; t += blockDim.x) (&whist[0][0])[t] = 0;
+        base[threadIdx.x] = offs[hist_slot(ch, c, threadIdx.x)];
+        __syncthreads();
+        uint64_t k[RS_IPT];
+        uint32_t v[RS_IPT], r[RS_IPT];
+        const int wbase = w * 32 * RS_IPT;
+#pragma unroll
+        for (int it = 0; it < RS_IPT; ++it) {
+            const int li = wbase + it * 32 + lane;     // warp-striped: (it, lane) is input order
+            const bool ok = li < ch.len;
+            k[it] = ok ? kin[ch.start + li] : 0ull;
+            v[it] = ok ? vin[ch.start + li] : 0u;
+            const uint32_t d = ok ? (uint32_t)(k[it] >> shift) & 0xffu : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = ok ? whist[w][d] : 0u;
+            __syncwarp();
+            if (ok && (peers & ltmask) == 0u) whist[w][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            r[it] = before + (uint32_t)__popc(peers & ltmask);
+        }
+        __syncthreads();
+        {   // exclusive prefix over the warps, per digit (warp order = input order)
+            const int d = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < RS_WARPS; ++ww) {
+                const uint32_t cnt = whist[ww][d];
+                whist[ww][d] = run;
+                run += cnt;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < RS_IPT; ++it) {
+            const int li = wbase + it * 32 + lane;
+            if (li < ch.len) {
+                const uint32_t d = (uint32_t)(k[it] >> shift) & 0xffu;
+                const uint32_t dst = base[d] + whist[w][d] + r[it];
+                kout[dst] = k[it];
+                vout[dst] = v[it];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Gather of the state into key order; also writes the pair-kernel copies of
+// the positions: FP32 hi/lo split (x = hi + lo to ~2^-48) or FP64 double4_32a.
+struct PermArgs {
+    const double *xin[7];
+    double *xout[7];
+    const int32_t *id_in;
+    int32_t *id_out;
+    const int32_t *orig_in;
+    int32_t *orig_out;
+    const uint32_t *src;
+    float4 *phi, *plo;
+    double4_32a *pd;
+    const int32_t *psys;
+    const SysBox *box;
+    int64_t N;
+};
+
+__global__ void __launch_bounds__(256) k_permute(PermArgs a, const Status *st)
+{
+    if (st->code) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = a.src[i];
+        double v[7];
+#pragma unroll
+        for (int f = 0; f < 7; ++f) {
+            v[f] = a.xin[f][j];
+            a.xout[f][i] = v[f];
+        }
+        if (a.id_in) a.id_out[i] = a.id_in[j];
+        a.orig_out[i] = a.orig_in[j];
+        if (a.phi) {
+            const SysBox b = a.box[a.psys[i]];
+            float h[3], l[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) grid_split(v[d], b.lo[d], b, h[d], l[d]);
+            a.phi[i] = make_float4(h[0], h[1], h[2], (float)v[6]);
+            a.plo[i] = make_float4(l[0], l[1], l[2], 0.0f);
+        }
+        if (a.pd) a.pd[i] = make_double4_32a(v[0], v[1], v[2], v[6]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Level-wise split. Nodes are numbered breadth first: level by level, and in
+// a level by system, then key. lvl[l] is the first node of level l.
+// ---------------------------------------------------------------------------
+__global__ void k_roots(int S, const int64_t *__restrict__ off, uint32_t *nfirst, uint32_t *ncount,
+                        uint32_t *nparent, uint32_t *nlevel, uint32_t *lvl, uint32_t *sysroot, const Status *st)
+{
+    if (st->code) return;
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < S) {
+        nfirst[s] = (uint32_t)off[s];
+        ncount[s] = (uint32_t)(off[s + 1] - off[s]);
+        nparent[s] = NONE;
+        nlevel[s] = 0;
+        sysroot[s] = (uint32_t)s;
+    }
+    if (s == 0) {
+        lvl[0] = 0;
+        for (int l = 1; l < LEVELS + 3; ++l) lvl[l] = (uint32_t)S;
+    }
+}
+
+__device__ __forceinline__ uint32_t digit_at(uint64_t key, int lev)
+{
+    return (uint32_t)(key >> (3 * (LEVELS - lev))) & 7u;
+}
+
+// Boundaries of the 8 octants (at level clev) inside the sorted range
+// [f, f + n): b[d] = first index whose digit is >= d. Seven interleaved
+// binary searches.
+__device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ key, uint32_t f, uint32_t n, int clev,
+                                              uint32_t b[9])
+{
+    uint32_t lo[7], hi[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+        lo[d] = f;
+        hi[d] = f + n;
+    }
+    for (uint32_t span = n; span > 0; span >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 7; ++d) {
+            if (lo[d] < hi[d]) {
+                const uint32_t mid = lo[d] + ((hi[d] - lo[d]) >> 1);
+                if (digit_at(key[mid], clev) < (uint32_t)(d + 1)) lo[d] = mid + 1;
+                else hi[d] = mid;
+            }
+        }
+    }
+    // the loop above runs log2(n)+1 rounds, enough for every search to close
+    b[0] = f;
+#pragma unroll
+    for (int d = 0; d < 7; ++d) b[d + 1] = lo[d];
+    b[8] = f + n;
+}
+
+__global__ void __launch_bounds__(256) k_level_count(int lev, const uint32_t *__restrict__ lvl,
+                                                     const uint32_t *__restrict__ nfirst,
+                                                     const uint32_t *__restrict__ ncount,
+                                                     const uint64_t *__restrict__ key, int n_leaf,
+                                                     uint32_t *__restrict__ nch, int64_t *d_n, const Status *st)
+{
+    if (st->code) return;
+    const uint32_t a = lvl[lev], e = lvl[lev + 1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = (int64_t)(e - a);
+    for (uint32_t c = a + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
+        const uint32_t cnt = ncount[c];
+        uint32_t k = 0;
+        if (cnt > (uint32_t)n_leaf && lev < LEVELS) {
+            uint32_t b[9];
+            octant_bounds(key, nfirst[c], cnt, lev + 1, b);
+#pragma unroll
+            for (int d = 0; d < 8; ++d) k += (b[d + 1] > b[d]) ? 1u : 0u;
+        }
+        nch[c - a] = k;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_level_emit(int lev, uint32_t *lvl, uint32_t *nfirst, uint32_t *ncount,
+                                                    const uint64_t *__restrict__ key, int n_leaf,
+                                                    const uint32_t *__restrict__ choff, const uint64_t *total,
+                                                    int64_t cap, uint32_t *nchild, uint32_t *nnch, uint32_t *nparent,
+                                                    uint32_t *nlevel, Status *st, int where)
+{
+    if (st->code) return;
+    const uint32_t a = lvl[lev], e = lvl[lev + 1];
+    const uint64_t tot = *total;
+    if ((int64_t)e + (int64_t)tot > cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            fail(st, HYBRID_ECAPACITY, where);
+            st->need[0] = 2 * ((int64_t)e + (int64_t)tot);
+        }
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[lev + 2] = e + (uint32_t)tot;
+    for (uint32_t c = a + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
+        const uint32_t cnt = ncount[c];
+        if (cnt > (uint32_t)n_leaf && lev < LEVELS) {
+            uint32_t b[9];
+            octant_bounds(key, nfirst[c], cnt, lev + 1, b);
+            const uint32_t base = e + choff[c - a];
+            uint32_t k = 0;
+#pragma unroll
+            for (int d = 0; d < 8; ++d) {
+                if (b[d + 1] > b[d]) {
+                    const uint32_t q = base + k++;
+                    nfirst[q] = b[d];
+                    ncount[q] = b[d + 1] - b[d];
+                    nparent[q] = c;
+                    nlevel[q] = (uint32_t)(lev + 1);
+                }
+            }
+            nchild[c] = base;
+            nnch[c] = k;
+        } else {
+            nchild[c] = NONE;
+            nnch[c] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Moments, bottom-up. A leaf sums its particles; the last child to finish
+// (counted with an atomic) sums the children into the parent. FP64.
+// B2 of a parent by the parallel-axis rule: sum_c [B2_c + M_c |com_c - com|^2].
+// Also writes the FP32 hi/lo copy of the centre of mass (walk and pair data).
+// ---------------------------------------------------------------------------
+struct MomArgs {
+    const uint32_t *lvl, *nfirst, *ncount, *nnch, *nchild, *nparent, *nlevel;
+    const double *x, *y, *z, *m;
+    const uint64_t *key;
+    const int32_t *psys;
+    const SysBox *box;
+    double *M, *cx, *cy, *cz, *B2;
+    float4 *nA, *nB;
+    uint32_t *done, *leafof;
+};
+
+__device__ __forceinline__ void cell_geom(const SysBox &b, uint64_t key, uint32_t lev, double o[3], double *side)
+{
+    const double sd = ldexp(b.L, -(int)lev);
+    // integer cell coordinate of the key prefix along each axis
+    uint32_t q[3] = {0, 0, 0};
+    for (uint32_t l = 1; l <= lev; ++l) {
+        const uint32_t d = digit_at(key, (int)l);
+        q[0] = (q[0] << 1) | ((d >> 2) & 1u);
+        q[1] = (q[1] << 1) | ((d >> 1) & 1u);
+        q[2] = (q[2] << 1) | (d & 1u);
+    }
+    for (int k = 0; k < 3; ++k) o[k] = __dadd_rn(b.lo[k], __dmul_rn((double)q[k], sd));
+    *side = sd;
+}
+
+__device__ __forceinline__ void store_com(const MomArgs &a, uint32_t c, double M, double c0, double c1, double c2,
+                                          double B2)
+{
+    a.M[c] = M;
+    a.cx[c] = c0;
+    a.cy[c] = c1;
+    a.cz[c] = c2;
+    a.B2[c] = B2;
+    const SysBox b = a.box[a.psys[a.nfirst[c]]];
+    float h[3], l[3];
+    grid_split(c0, b.lo[0], b, h[0], l[0]);
+    grid_split(c1, b.lo[1], b, h[1], l[1]);
+    grid_split(c2, b.lo[2], b, h[2], l[2]);
+    a.nA[c] = make_float4(h[0], h[1], h[2], (float)M);
+    a.nB[c] = make_float4(l[0], l[1], l[2], 0.0f);
+}
+
+__global__ void __launch_bounds__(256) k_moments(MomArgs a, const Status *st)
+{
+    if (st->code) return;
+    const uint32_t total = a.lvl[LEVELS + 1];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+        if (a.nnch[c] != 0) continue;
+        const uint32_t f = a.nfirst[c], n = a.ncount[c];
+        double M = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (uint32_t i = f; i < f + n; ++i) {
+            const double mi = a.m[i];
+            M += mi;
+            s0 += mi * a.x[i];
+            s1 += mi * a.y[i];
+            s2 += mi * a.z[i];
+            a.leafof[i] = c;
+        }
+        double c0, c1, c2;
+        if (M > 0.0) {
+            c0 = s0 / M;
+            c1 = s1 / M;
+            c2 = s2 / M;
+        } else {   // massless cell: its geometric centre
+            double o[3], sd;
+            cell_geom(a.box[a.psys[f]], a.key[f], a.nlevel[c], o, &sd);
+            c0 = o[0] + 0.5 * sd;
+            c1 = o[1] + 0.5 * sd;
+            c2 = o[2] + 0.5 * sd;
+        }
+        double B2 = 0.0;
+        for (uint32_t i = f; i < f + n; ++i) {
+            const double d0 = a.x[i] - c0, d1 = a.y[i] - c1, d2 = a.z[i] - c2;
+            B2 += a.m[i] * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        store_com(a, c, M, c0, c1, c2, B2);
+        // climb while this thread completes the last child of the parent
+        uint32_t p = a.nparent[c];
+        while (p != NONE) {
+            __threadfence();
+            const uint32_t k = a.nnch[p];
+            if (atomicAdd(&a.done[p], 1u) != k - 1u) break;
+            __threadfence();
+            const uint32_t ch = a.nchild[p];
+            double Mp = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            for (uint32_t j = 0; j < k; ++j) {
+                const double Mj = __ldcg(&a.M[ch + j]);
+                Mp += Mj;
+                t0 += Mj * __ldcg(&a.cx[ch + j]);
+                t1 += Mj * __ldcg(&a.cy[ch + j]);
+                t2 += Mj * __ldcg(&a.cz[ch + j]);
+            }
+            double p0, p1, p2;
+            if (Mp > 0.0) {
+                p0 = t0 / Mp;
+                p1 = t1 / Mp;
+                p2 = t2 / Mp;
+            } else {
+                double o[3], sd;
+                const uint32_t fp = a.nfirst[p];
+                cell_geom(a.box[a.psys[fp]], a.key[fp], a.nlevel[p], o, &sd);
+                p0 = o[0] + 0.5 * sd;
+                p1 = o[1] + 0.5 * sd;
+                p2 = o[2] + 0.5 * sd;
+            }
+            double Bp = 0.0;
+            for (uint32_t j = 0; j < k; ++j) {
+                const double Mj = __ldcg(&a.M[ch + j]);
+                const double d0 = __ldcg(&a.cx[ch + j]) - p0, d1 = __ldcg(&a.cy[ch + j]) - p1,
+                             d2 = __ldcg(&a.cz[ch + j]) - p2;
+                Bp += __ldcg(&a.B2[ch + j]) + Mj * (d0 * d0 + d1 * d1 + d2 * d2);
+            }
+            store_com(a, p, Mp, p0, p1, p2, Bp);
+            p = a.nparent[p];
+        }
+    }
+}
+
+// b_max = max over members of |x_i - com|: every particle visits its
+// ancestors level by level; lanes of a warp that share a node reduce with a
+// segmented max (sorted particles: a node's lanes are contiguous), then one
+// atomic max per run. F64: FP64 distance; else FP32 from the hi/lo copies.
+template <bool F64>
+__global__ void __launch_bounds__(256) k_bmax(int64_t N, const uint32_t *__restrict__ leafof,
+                                              const uint32_t *__restrict__ nparent,
+                                              const uint32_t *__restrict__ nlevel, const double *__restrict__ x,
+                                              const double *__restrict__ y, const double *__restrict__ z,
+                                              const double *__restrict__ cx, const double *__restrict__ cy,
+                                              const double *__restrict__ cz, const float4 *__restrict__ phi,
+                                              const float4 *__restrict__ plo, const float4 *__restrict__ nA,
+                                              const float4 *__restrict__ nB, unsigned long long *bmax,
+                                              const Status *st)
+{
+    if (st->code) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarp_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t wb = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wb * 32 < N; wb += nwarp_total) {
+        const int64_t i = wb * 32 + lane;
+        const bool ok = i < N;
+        uint32_t c = ok ? leafof[i] : NONE;
+        int lev = ok ? (int)nlevel[c] : -1;
+        int maxlev = lev;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) maxlev = max(maxlev, __shfl_xor_sync(0xffffffffu, maxlev, o));
+        double px = 0, py = 0, pz = 0;
+        float4 ph = make_float4(0, 0, 0, 0), pl = ph;
+        if (ok) {
+            if (F64) {
+                px = x[i];
+                py = y[i];
+                pz = z[i];
+            } else {
+                ph = phi[i];
+                pl = plo[i];
+            }
+        }
+        for (int L = maxlev; L >= 0; --L) {
+            const bool act = (lev == L);
+            double dist = 0.0;
+            if (act) {
+                if (F64) {
+                    const double d0 = px - cx[c], d1 = py - cy[c], d2 = pz - cz[c];
+                    dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                } else {
+                    const float4 A = nA[c], B = nB[c];
+                    const float d0 = (ph.x - A.x) + (pl.x - B.x);
+                    const float d1 = (ph.y - A.y) + (pl.y - B.y);
+                    const float d2 = (ph.z - A.z) + (pl.z - B.z);
+                    dist = (double)sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                }
+            }
+            const uint32_t keyv = act ? c : NONE;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double du = __shfl_up_sync(0xffffffffu, dist, o);
+                const uint32_t ku = __shfl_up_sync(0xffffffffu, keyv, o);
+                if (lane >= o && ku == keyv) dist = fmax(dist, du);
+            }
+            const uint32_t kd = __shfl_down_sync(0xffffffffu, keyv, 1);
+            if (act && (lane == 31 || kd != keyv))
+                atomicMax(&bmax[c], (unsigned long long)__double_as_longlong(dist));
+            if (act) {
+                c = nparent[c];
+                lev = L - 1;
+            }
+        }
+    }
+}
+
+// Per node: geometry, delta, MAC radius, walk criteria and packed topology.
+struct FinArgs {
+    const uint32_t *lvl, *nfirst, *ncount, *nnch, *nchild, *nlevel;
+    const uint64_t *key;
+    const int32_t *psys;
+    const SysBox *box;
+    const SysParams *sp;
+    const double *M, *cx, *cy, *cz, *B2;
+    const unsigned long long *bmax;
+    float2 *crit;
+    uint4 *topo;
+    double4_32a *nD;
+    double *rb, *hr, *delta, *side, *org;
+};
+
+__global__ void __launch_bounds__(256) k_finalize(FinArgs a, const Status *st)
+{
+    if (st->code) return;
+    const uint32_t total = a.lvl[LEVELS + 1];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+        const uint32_t f = a.nfirst[c];
+        const int s = a.psys[f];
+        const SysParams P = a.sp[s];
+        double o[3], sd;
+        cell_geom(a.box[s], a.key[f], a.nlevel[c], o, &sd);
+        const double ctr0 = o[0] + 0.5 * sd, ctr1 = o[1] + 0.5 * sd, ctr2 = o[2] + 0.5 * sd;
+        const double e0 = a.cx[c] - ctr0, e1 = a.cy[c] - ctr1, e2 = a.cz[c] - ctr2;
+        const double delta = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+        const double bm = __longlong_as_double((long long)a.bmax[c]);
+        double rb;
+        if (P.mac == 1) rb = 0.5 * bm + sqrt(0.25 * bm * bm + sqrt(3.0 * a.B2[c] / P.a_err));
+        else rb = (P.theta > 0.0) ? sd / P.theta + delta : INFINITY;
+        const double hr = P.R2 + bm;   // Eq. (15) radius
+        const double sacc = fmax(rb, hr);
+        a.crit[c] = make_float2((float)(sacc * sacc), P.has_hard ? (float)(hr * hr) : -1.0f);
+        const uint32_t k = a.nnch[c];
+        a.topo[c] = make_uint4(k ? a.nchild[c] : NONE, k, f, a.ncount[c]);
+        a.nD[c] = make_double4_32a(a.cx[c], a.cy[c], a.cz[c], a.M[c]);
+        a.rb[c] = rb;
+        a.hr[c] = hr;
+        a.delta[c] = delta;
+        a.side[c] = sd;
+        a.org[3 * (size_t)c + 0] = o[0];
+        a.org[3 * (size_t)c + 1] = o[1];
+        a.org[3 * (size_t)c + 2] = o[2];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sink groups: first cells (from the root) with count <= n_crit, or leaves.
+// Marked at their first particle, compacted in particle order.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_group_flag(const uint32_t *__restrict__ lvl,
+                                                    const uint32_t *__restrict__ nfirst,
+                                                    const uint32_t *__restrict__ ncount,
+                                                    const uint32_t *__restrict__ nnch,
+                                                    const uint32_t *__restrict__ nparent, int n_crit,
+                                                    uint32_t *__restrict__ gflag, const Status *st)
+{
+    if (st->code) return;
+    const uint32_t total = lvl[LEVELS + 1];
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
+        const bool stop = ncount[c] <= (uint32_t)n_crit || nnch[c] == 0;
+        const uint32_t p = nparent[c];
+        const bool parent_goes_on = (p == NONE) || (ncount[p] > (uint32_t)n_crit);
+        if (stop && parent_goes_on) gflag[nfirst[c]] = c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_group_mark(int64_t N, const uint32_t *__restrict__ gflag,
+                                                    uint32_t *__restrict__ gscan, const Status *st)
+{
+    if (st->code) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        gscan[i] = gflag[i] != NONE ? 1u : 0u;
+}
+
+__global__ void __launch_bounds__(256) k_group_compact(int64_t N, const uint32_t *__restrict__ gflag,
+                                                       const uint32_t *__restrict__ gscan,
+                                                       const uint32_t *__restrict__ ncount,
+                                                       const int32_t *__restrict__ psys, uint32_t *gnode,
+                                                       uint32_t *gfirst, uint32_t *gcount, uint32_t *gsys,
+                                                       const uint64_t *total, int64_t *ngroups, const Status *st)
+{
+    if (st->code) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ngroups = (int64_t)*total;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = gflag[i];
+        if (c != NONE) {
+            const uint32_t g = gscan[i];
+            gnode[g] = c;
+            gfirst[g] = (uint32_t)i;
+            gcount[g] = ncount[c];
+            gsys[g] = (uint32_t)psys[i];
+        }
+    }
+}
+
+// One warp per group: box of the members (FP64, exact min/max), its centre
+// as an FP32 hi/lo pair and its half extents rounded up.
+__global__ void __launch_bounds__(256) k_group_box(const int64_t *__restrict__ ngroups,
+                                                   const uint32_t *__restrict__ gfirst,
+                                                   const uint32_t *__restrict__ gcount, const double *__restrict__ x,
+                                                   const double *__restrict__ y, const double *__restrict__ z,
+                                                   const int32_t *__restrict__ psys, const SysBox *__restrict__ box,
+                                                   double *glo, double *ghi, GroupF *gF, const Status *st)
+{
+    if (st->code) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = *ngroups;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
+        const uint32_t f = gfirst[g], n = gcount[g];
+        double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        for (uint32_t i = f + lane; i < f + n; i += 32) {
+            const double p0 = x[i], p1 = y[i], p2 = z[i];
+            v[0] = fmin(v[0], p0);
+            v[1] = fmin(v[1], p1);
+            v[2] = fmin(v[2], p2);
+            v[3] = fmax(v[3], p0);
+            v[4] = fmax(v[4], p1);
+            v[5] = fmax(v[5], p2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) v[j] = fmin(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+#pragma unroll
+            for (int j = 3; j < 6; ++j) v[j] = fmax(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+        }
+        if (lane == 0) {
+            const SysBox b = box[psys[f]];
+            float hc[3], lc[3], he[3];
+            for (int d = 0; d < 3; ++d) {
+                glo[3 * g + d] = v[d];
+                ghi[3 * g + d] = v[d + 3];
+                const double cc = 0.5 * (v[d] + v[d + 3]) - b.lo[d];   // relative to the root corner
+                hc[d] = (float)cc;
+                lc[d] = (float)(cc - (double)hc[d]);
+                he[d] = __double2float_ru(0.5 * (v[d + 3] - v[d]));
+            }
+            GroupF G;
+            G.c_hi = make_float4(hc[0], hc[1], hc[2], he[0]);
+            G.c_lo = make_float4(lc[0], lc[1], lc[2], he[1]);
+            G.hz_root = make_float2(he[2], 0.0f);
+            gF[g] = G;
+        }
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int grid_for(hybrid_ctx *c, int64_t work, int threads, int per_sm = 8)
+{
+    int64_t g = (work + threads - 1) / threads;
+    g = std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)c->nsm * per_sm));
+    return (int)g;
+}
+
+void launch_box(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    cudaMemsetAsync(c->boxmin.p, 0xff, (size_t)3 * c->S * sizeof(unsigned long long), c->st);
+    cudaMemsetAsync(c->boxmax.p, 0x00, (size_t)3 * c->S * sizeof(unsigned long long), c->st);
+    k_box<<<std::min(c->nchunks, c->nsm * 8), 256, 0, c->st>>>(
+        (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const Chunk *)c->chunks_dev.p,
+        c->nchunks, (unsigned long long *)c->boxmin.p, (unsigned long long *)c->boxmax.p, st);
+    k_box_final<<<(c->S + 127) / 128, 128, 0, c->st>>>(c->S, (const unsigned long long *)c->boxmin.p,
+                                                       (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, st);
+    c->launches += 2;
+}
+
+void launch_keys_sort_permute(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    const int64_t N = c->N;
+    uint64_t *k0 = (uint64_t *)c->keys[0].p, *k1 = (uint64_t *)c->keys[1].p;
+    uint32_t *v0 = (uint32_t *)c->vals[0].p, *v1 = (uint32_t *)c->vals[1].p;
+    k_keys<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const double *)c->x[0].p, (const double *)c->x[1].p,
+                                                    (const double *)c->x[2].p, (const int32_t *)c->psys.p,
+                                                    (const SysBox *)c->box.p, k0, v0, st);
+    c->launches++;
+    const int grid = std::min(c->nchunks, c->nsm * 4);
+    uint32_t *hist = (uint32_t *)c->hist.p;
+    for (int pass = 0; pass < 8; ++pass) {
+        const int shift = 8 * pass;
+        k_radix_hist<<<grid, 256, 0, c->st>>>(k0, (const Chunk *)c->chunks_dev.p, c->nchunks, shift, hist, st);
+        c->launches++;
+        scan_u32(c, hist, (int64_t)c->nchunks * 256, nullptr, (int64_t)c->nchunks * 256, nullptr);
+        k_radix_scatter<<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, (const Chunk *)c->chunks_dev.p, c->nchunks, shift,
+                                                  hist, st);
+        c->launches++;
+        std::swap(k0, k1);
+        std::swap(v0, v1);
+    }
+    // after 8 passes the sorted keys/values are back in buffer 0
+    PermArgs a;
+    for (int f = 0; f < 7; ++f) {
+        a.xin[f] = (const double *)c->x[f].p;
+        a.xout[f] = (double *)c->xa[f].p;
+    }
+    a.id_in = (const int32_t *)c->id.p;
+    a.id_out = (int32_t *)c->ida.p;
+    a.orig_in = (const int32_t *)c->orig.p;
+    a.orig_out = (int32_t *)c->origa.p;
+    a.src = v0;
+    a.phi = c->p.precision == 1 ? (float4 *)c->phi.p : nullptr;
+    a.plo = c->p.precision == 1 ? (float4 *)c->plo.p : nullptr;
+    a.pd = c->p.precision == 0 ? (double4_32a *)c->pd.p : nullptr;
+    a.psys = (const int32_t *)c->psys.p;
+    a.box = (const SysBox *)c->box.p;
+    a.N = N;
+    k_permute<<<grid_for(c, N, 256), 256, 0, c->st>>>(a, st);
+    c->launches++;
+    for (int f = 0; f < 7; ++f) std::swap(c->x[f], c->xa[f]);
+    std::swap(c->id, c->ida);
+    std::swap(c->orig, c->origa);
+}
+
+bool launch_build_levels(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    uint32_t *lvl = (uint32_t *)c->lvl.p;
+    k_roots<<<(c->S + 127) / 128, 128, 0, c->st>>>(c->S, (const int64_t *)c->off_dev.p, (uint32_t *)c->nfirst.p,
+                                                   (uint32_t *)c->ncount.p, (uint32_t *)c->nparent.p,
+                                                   (uint32_t *)c->nlevel.p, lvl, (uint32_t *)c->sysroot.p, st);
+    c->launches++;
+    int64_t *d_n = (int64_t *)((char *)c->lvl.p + 64 * sizeof(uint32_t));
+    uint64_t *d_tot = (uint64_t *)((char *)c->lvl.p + 64 * sizeof(uint32_t) + 64);
+    const uint64_t *keys = (const uint64_t *)c->keys[0].p;
+    const int grid = grid_for(c, c->capNodes, 256, 4);
+    for (int lev = 0; lev <= LEVELS; ++lev) {
+        k_level_count<<<grid, 256, 0, c->st>>>(lev, lvl, (const uint32_t *)c->nfirst.p, (const uint32_t *)c->ncount.p,
+                                                keys, c->p.n_leaf, (uint32_t *)c->nchtmp.p, d_n, st);
+        scan_u32(c, (uint32_t *)c->nchtmp.p, 0, d_n, c->capNodes, d_tot);
+        k_level_emit<<<grid, 256, 0, c->st>>>(lev, lvl, (uint32_t *)c->nfirst.p, (uint32_t *)c->ncount.p, keys,
+                                               c->p.n_leaf, (const uint32_t *)c->nchtmp.p, d_tot, c->capNodes,
+                                               (uint32_t *)c->nchild.p, (uint32_t *)c->nnch.p, (uint32_t *)c->nparent.p,
+                                               (uint32_t *)c->nlevel.p, st, c->op);
+        c->launches += 2;
+    }
+    return true;
+}
+
+void launch_moments(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    const int grid = grid_for(c, c->capNodes, 256, 8);
+    cudaMemsetAsync(c->ndone.p, 0, (size_t)c->capNodes * sizeof(uint32_t), c->st);
+    cudaMemsetAsync(c->nbmax.p, 0, (size_t)c->capNodes * sizeof(unsigned long long), c->st);
+    MomArgs a;
+    a.lvl = (const uint32_t *)c->lvl.p;
+    a.nfirst = (const uint32_t *)c->nfirst.p;
+    a.ncount = (const uint32_t *)c->ncount.p;
+    a.nnch = (const uint32_t *)c->nnch.p;
+    a.nchild = (const uint32_t *)c->nchild.p;
+    a.nparent = (const uint32_t *)c->nparent.p;
+    a.nlevel = (const uint32_t *)c->nlevel.p;
+    a.x = (const double *)c->x[0].p;
+    a.y = (const double *)c->x[1].p;
+    a.z = (const double *)c->x[2].p;
+    a.m = (const double *)c->x[6].p;
+    a.key = (const uint64_t *)c->keys[0].p;
+    a.psys = (const int32_t *)c->psys.p;
+    a.box = (const SysBox *)c->box.p;
+    a.M = (double *)c->nM.p;
+    a.cx = (double *)c->ncx.p;
+    a.cy = (double *)c->ncy.p;
+    a.cz = (double *)c->ncz.p;
+    a.B2 = (double *)c->nB2.p;
+    a.nA = (float4 *)c->nA.p;
+    a.nB = (float4 *)c->nB.p;
+    a.done = (uint32_t *)c->ndone.p;
+    a.leafof = (uint32_t *)c->leafof.p;
+    k_moments<<<grid, 256, 0, c->st>>>(a, st);
+    const int gridp = grid_for(c, c->N, 256, 8);
+    if (c->p.precision == 0)
+        k_bmax<true><<<gridp, 256, 0, c->st>>>(
+            c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, a.x, a.y,
+            a.z, a.cx, a.cy, a.cz, nullptr, nullptr, nullptr, nullptr, (unsigned long long *)c->nbmax.p, st);
+    else
+        k_bmax<false><<<gridp, 256, 0, c->st>>>(
+            c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, (const float4 *)c->phi.p, (const float4 *)c->plo.p, a.nA, a.nB,
+            (unsigned long long *)c->nbmax.p, st);
+    FinArgs f;
+    f.lvl = a.lvl;
+    f.nfirst = a.nfirst;
+    f.ncount = a.ncount;
+    f.nnch = a.nnch;
+    f.nchild = a.nchild;
+    f.nlevel = a.nlevel;
+    f.key = a.key;
+    f.psys = a.psys;
+    f.box = a.box;
+    f.sp = (const SysParams *)c->sp_dev.p;
+    f.M = a.M;
+    f.cx = a.cx;
+    f.cy = a.cy;
+    f.cz = a.cz;
+    f.B2 = a.B2;
+    f.bmax = (const unsigned long long *)c->nbmax.p;
+    f.crit = (float2 *)c->ncrit.p;
+    f.topo = (uint4 *)c->ntopo.p;
+    f.nD = (double4_32a *)c->nD.p;
+    f.rb = (double *)c->nrb.p;
+    f.hr = (double *)c->nhr.p;
+    f.delta = (double *)c->ndelta.p;
+    f.side = (double *)c->nside.p;
+    f.org = (double *)c->norg.p;
+    k_finalize<<<grid, 256, 0, c->st>>>(f, st);
+    c->launches += 3;
+}
+
+void launch_groups(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    const int64_t N = c->N;
+    cudaMemsetAsync(c->gflag.p, 0xff, (size_t)N * sizeof(uint32_t), c->st);
+    k_group_flag<<<grid_for(c, c->capNodes, 256), 256, 0, c->st>>>(
+        (const uint32_t *)c->lvl.p, (const uint32_t *)c->nfirst.p, (const uint32_t *)c->ncount.p,
+        (const uint32_t *)c->nnch.p, (const uint32_t *)c->nparent.p, c->p.n_crit, (uint32_t *)c->gflag.p, st);
+    k_group_mark<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const uint32_t *)c->gflag.p, (uint32_t *)c->gscan.p, st);
+    uint64_t *d_tot = (uint64_t *)((char *)c->lvl.p + 64 * sizeof(uint32_t) + 64 + 8);
+    scan_u32(c, (uint32_t *)c->gscan.p, N, nullptr, N, d_tot);
+    k_group_compact<<<grid_for(c, N, 256), 256, 0, c->st>>>(
+        N, (const uint32_t *)c->gflag.p, (const uint32_t *)c->gscan.p, (const uint32_t *)c->ncount.p,
+        (const int32_t *)c->psys.p, (uint32_t *)c->gnode.p, (uint32_t *)c->gfirst.p, (uint32_t *)c->gcount.p,
+        (uint32_t *)c->gsys.p, d_tot, (int64_t *)c->ngroups_dev.p, st);
+    k_group_box<<<grid_for(c, N * 32 / 16, 256), 256, 0, c->st>>>(
+        (const int64_t *)c->ngroups_dev.p, (const uint32_t *)c->gfirst.p, (const uint32_t *)c->gcount.p,
+        (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const int32_t *)c->psys.p,
+        (const SysBox *)c->box.p, (double *)c->glo.p, (double *)c->ghi.p, (GroupF *)c->gF.p, st);
+    c->launches += 4;
+}
+
+}  // namespace hy

@@ -1,0 +1,292 @@
+// walk.cu -- grouped tree walk that emits interaction lists (Sec. II-B
+// traversal rule; Eq. 11 with the box of a sink group in place of the n_vec
+// sinks; Eq. 15 for the hard neighbours and for the cutoff test).
+//
+// One warp walks one group at a time, starting at its system's root. Each
+// iteration pops up to 32 pending cells (one per lane) from a per-warp stack,
+// tests them, and with warp ballots/scans appends:
+//   soft cells      taken whole: r >= r_b and r >= R2 + b_max,
+//   soft particles  members of leaves that the soft walk opens,
+//   hard particles  members of leaves with r < R2 + b_max,
+// and pushes the children of opened cells. r is the distance from the cell's
+// centre of mass to the group box. The count pass sizes every list, a scan
+// turns counts into offsets, and the fill pass writes the lists.
+#include "hy_internal.cuh"
+
+namespace hy {
+
+namespace {
+
+constexpr int WALK_THREADS = 128;
+
+struct WalkArgs {
+    const int64_t *ngroups;
+    const uint32_t *gnode, *gsys;
+    const GroupF *gF;
+    const double *glo, *ghi;
+    const uint32_t *sysroot;
+    const SysParams *sp;
+    const uint4 *topo;
+    const float4 *nA, *nB;
+    const float2 *crit;
+    const double4_32a *nD;
+    const double *rb, *hr;
+    uint64_t *cnt;          // count pass: counts; fill pass: offsets ([3][ng] + total)
+    int64_t *d_n3;
+    const uint64_t *list_total;
+    uint32_t *list;
+    int64_t cap_list;
+    uint32_t *stack;
+    int64_t cap_stack;
+    unsigned long long *counter;
+    int mode;
+    Status *st;
+    int where;
+};
+
+__device__ __forceinline__ void fail(Status *st, int code, int where)
+{
+    atomicCAS(&st->code, 0, code);
+    st->where = where;
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    total = __shfl_sync(0xffffffffu, inc, 31);
+    return inc - v;
+}
+
+// distance from p to the box [lo, hi], per axis max(lo - p, 0, p - hi)
+__device__ __forceinline__ double dist_box_f64(double p0, double p1, double p2, const double *lo, const double *hi)
+{
+    const double p[3] = {p0, p1, p2};
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double g = 0.0;
+        const double a = lo[d] - p[d];
+        const double b = p[d] - hi[d];
+        if (a > g) g = a;
+        if (b > g) g = b;
+        s += g * g;
+    }
+    return sqrt(s);
+}
+
+template <bool F64, bool FILL>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
+{
+    Status *st = a.st;
+    if (st->code) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const int64_t ng = *a.ngroups;
+    if (!FILL && blockIdx.x == 0 && threadIdx.x == 0) *a.d_n3 = 3 * ng;
+    if (FILL) {
+        const uint64_t total = *a.list_total;
+        if ((int64_t)total > a.cap_list) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                fail(st, HYBRID_ECAPACITY, a.where);
+                st->need[1] = (int64_t)total;
+            }
+            return;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.cnt[3 * ng] = total;
+    }
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t *stk = a.stack + gw * a.cap_stack;
+    const bool want_soft = a.mode & 1, want_hard = (a.mode >> 1) & 1;
+
+    for (;;) {
+        unsigned long long gg = 0;
+        if (lane == 0) gg = atomicAdd(a.counter, 1ull);
+        const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gg, 0);
+        if (g >= ng) break;
+        const uint32_t s = a.gsys[g];
+        const bool wh0 = want_hard && a.sp[s].has_hard;
+        float cx = 0, cy = 0, cz = 0, lx = 0, ly = 0, lz = 0, hx = 0, hy = 0, hz = 0;
+        double blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+        if (F64) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                blo[d] = a.glo[3 * g + d];
+                bhi[d] = a.ghi[3 * g + d];
+            }
+        } else {
+            const GroupF G = a.gF[g];
+            cx = G.c_hi.x;
+            cy = G.c_hi.y;
+            cz = G.c_hi.z;
+            hx = G.c_hi.w;
+            lx = G.c_lo.x;
+            ly = G.c_lo.y;
+            lz = G.c_lo.z;
+            hy = G.c_lo.w;
+            hz = G.hz_root.x;
+        }
+        uint64_t nc = 0, np = 0, nh = 0, oc = 0, op = 0, oh = 0;
+        if (FILL) {
+            oc = a.cnt[g];
+            op = a.cnt[ng + g];
+            oh = a.cnt[2 * ng + g];
+        }
+        int64_t sp = 0;
+        if (want_soft || wh0) {
+            if (lane == 0) stk[0] = a.sysroot[s] | ((uint32_t)want_soft << 30) | ((uint32_t)wh0 << 31);
+            sp = 1;
+        }
+        __syncwarp();
+        bool overflow = false;
+        while (sp > 0) {
+            const int take = (int)(sp < 32 ? sp : 32);
+            uint32_t e = 0;
+            if (lane < take) e = stk[sp - take + lane];
+            sp -= take;
+            __syncwarp();
+            const bool valid = lane < take;
+            const uint32_t c = e & 0x3fffffffu;
+            const bool ws = (e >> 30) & 1u, wh = (e >> 31) & 1u;
+            bool accept = false, near = false;
+            uint4 T = make_uint4(NONE, 0, 0, 0);
+            if (valid) {
+                T = a.topo[c];
+                if (F64) {
+                    const double4_32a D = a.nD[c];
+                    const double d = dist_box_f64(D.x, D.y, D.z, blo, bhi);
+                    const double hr = a.hr[c];
+                    accept = (d >= a.rb[c]) && (d >= hr);
+                    near = wh && (d < hr);
+                } else {
+                    const float4 A = a.nA[c], B = a.nB[c];
+                    const float2 cr = a.crit[c];
+                    const float rx = fmaxf(fabsf((A.x - cx) + (B.x - lx)) - hx, 0.0f);
+                    const float ry = fmaxf(fabsf((A.y - cy) + (B.y - ly)) - hy, 0.0f);
+                    const float rz = fmaxf(fabsf((A.z - cz) + (B.z - lz)) - hz, 0.0f);
+                    const float d2 = rx * rx + ry * ry + rz * rz;
+                    accept = d2 >= cr.x;
+                    near = wh && (d2 < cr.y);
+                }
+            }
+            const bool leaf = (T.y == 0);
+            const bool take_cell = valid && ws && accept;
+            const bool soft_leaf = valid && ws && !accept && leaf;
+            const bool hard_leaf = valid && near && leaf;
+            const bool open_s = ws && !accept;
+            const bool open = valid && !leaf && (open_s || near);
+            // taken cells
+            const unsigned bm = __ballot_sync(0xffffffffu, take_cell);
+            if (FILL && take_cell) a.list[oc + nc + __popc(bm & ltmask)] = c;
+            nc += (uint64_t)__popc(bm);
+            // soft particles
+            {
+                uint32_t tot;
+                const uint32_t k = soft_leaf ? T.w : 0u;
+                const uint32_t ex = warp_excl_scan(k, tot);
+                if (FILL && soft_leaf) {
+                    uint32_t *dst = a.list + op + np + ex;
+                    for (uint32_t j = 0; j < k; ++j) dst[j] = T.z + j;
+                }
+                np += tot;
+            }
+            // hard particles
+            {
+                uint32_t tot;
+                const uint32_t k = hard_leaf ? T.w : 0u;
+                const uint32_t ex = warp_excl_scan(k, tot);
+                if (FILL && hard_leaf) {
+                    uint32_t *dst = a.list + oh + nh + ex;
+                    for (uint32_t j = 0; j < k; ++j) dst[j] = T.z + j;
+                }
+                nh += tot;
+            }
+            // children of opened cells
+            {
+                uint32_t tot;
+                const uint32_t k = open ? T.y : 0u;
+                const uint32_t ex = warp_excl_scan(k, tot);
+                if (sp + (int64_t)tot > a.cap_stack) {
+                    overflow = true;
+                    break;
+                }
+                if (open) {
+                    const uint32_t fl = ((uint32_t)open_s << 30) | ((uint32_t)near << 31);
+                    for (uint32_t j = 0; j < k; ++j) stk[sp + ex + j] = (T.x + j) | fl;
+                }
+                sp += tot;
+            }
+            __syncwarp();
+        }
+        if (overflow) {
+            if (lane == 0) {
+                fail(st, HYBRID_ECAPACITY, a.where);
+                st->need[2] = 2 * a.cap_stack;
+            }
+            break;
+        }
+        if (!FILL && lane == 0) {
+            a.cnt[g] = nc;
+            a.cnt[ng + g] = np;
+            a.cnt[2 * ng + g] = nh;
+        }
+    }
+}
+
+}  // namespace
+
+void launch_walk(hybrid_ctx *c, int mode)
+{
+    Status *st = status_dev(c);
+    WalkArgs a;
+    a.ngroups = (const int64_t *)c->ngroups_dev.p;
+    a.gnode = (const uint32_t *)c->gnode.p;
+    a.gsys = (const uint32_t *)c->gsys.p;
+    a.gF = (const GroupF *)c->gF.p;
+    a.glo = (const double *)c->glo.p;
+    a.ghi = (const double *)c->ghi.p;
+    a.sysroot = (const uint32_t *)c->sysroot.p;
+    a.sp = (const SysParams *)c->sp_dev.p;
+    a.topo = (const uint4 *)c->ntopo.p;
+    a.nA = (const float4 *)c->nA.p;
+    a.nB = (const float4 *)c->nB.p;
+    a.crit = (const float2 *)c->ncrit.p;
+    a.nD = (const double4_32a *)c->nD.p;
+    a.rb = (const double *)c->nrb.p;
+    a.hr = (const double *)c->nhr.p;
+    a.cnt = (uint64_t *)c->lcnt.p;
+    int64_t *d_n3 = (int64_t *)c->counter.p + 4;
+    uint64_t *d_total = (uint64_t *)c->counter.p + 5;
+    a.d_n3 = d_n3;
+    a.list_total = d_total;
+    a.list = (uint32_t *)c->list.p;
+    a.cap_list = c->capList;
+    a.stack = (uint32_t *)c->stack.p;
+    a.cap_stack = c->capStack;
+    a.mode = mode;
+    a.st = st;
+    a.where = c->op;
+    const int grid = c->walk_warps * 32 / WALK_THREADS;
+    cudaEvent_t e0 = nullptr;
+    prof_begin(c, PROF_WALK, &e0);
+    // count pass
+    cudaMemsetAsync(c->counter.p, 0, 2 * sizeof(unsigned long long), c->st);
+    a.counter = (unsigned long long *)c->counter.p;
+    if (c->p.precision == 0) k_walk<true, false><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    else k_walk<false, false><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    scan_u64(c, (uint64_t *)c->lcnt.p, 0, d_n3, 3 * c->capGroups, d_total);
+    // fill pass
+    a.counter = (unsigned long long *)c->counter.p + 1;
+    if (c->p.precision == 0) k_walk<true, true><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    else k_walk<false, true><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    prof_end(c, PROF_WALK, e0);
+    c->launches += 2;
+    c->last_walk_mode = mode;
+}
+
+}  // namespace hy

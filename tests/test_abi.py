@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads on a machine without a GPU, and
+exports every entry point include/hybrid.h declares. No compute call is made."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1406_6158_gb300 import build, hybrid
+    build.build()
+    return hybrid.load()
+
+
+def declared():
+    text = open(os.path.join(ROOT, "include", "hybrid.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hybrid_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_path():
+    names = declared()
+    for f in ("hybrid_build_tree", "hybrid_soft_force", "hybrid_hard_force", "hybrid_kick", "hybrid_drift",
+              "hybrid_step", "hybrid_step_batched", "hybrid_create", "hybrid_destroy"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1406_6158_gb300 import hybrid
+    for name in declared():
+        assert hasattr(lib, name), name
+    assert sorted(hybrid.EXPORTS) == declared()
+
+
+def test_library_is_sm103a(lib):
+    # the fatbinary carries sm_103a code; checked from the build flags, not by decoding the binary
+    from paper_1406_6158_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_invalid_params_rejected_without_gpu(lib):
+    from paper_1406_6158_gb300 import hybrid
+    bad = [
+        dict(eps=-1.0), dict(R1=0.2, R2=0.1), dict(R1=0.1, R2=0.1), dict(n_hard=0), dict(n_leaf=0),
+        dict(n_crit=0), dict(precision=2), dict(mac=1, a_err=0.0), dict(theta=-0.1),
+    ]
+    for kw in bad:
+        p = hybrid.Params(**kw).c()
+        h = C.c_void_p()
+        assert lib.hybrid_create(C.byref(h), C.byref(p), None) == hybrid.EINVAL, kw
+        assert not h.value
+    assert lib.hybrid_create(None, None, None) == hybrid.EINVAL
+    assert lib.hybrid_destroy(None) == hybrid.OK
+    assert lib.hybrid_launch_count(None) == 0
+
+
+def test_struct_layout_matches_header():
+    # hybrid_params: 7 doubles + 7 int32 = 84 -> padded to 88; hybrid_system: int64 + 14 pointers + pointer + int32
+    from paper_1406_6158_gb300 import hybrid
+    assert C.sizeof(hybrid.hybrid_params) == 88
+    assert C.sizeof(hybrid.hybrid_system) == 8 + 8 * 15 + 8

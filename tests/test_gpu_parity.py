@@ -1,0 +1,326 @@
+"""GPU path vs the FP64 oracle, through the C-ABI (libhybrid.so).
+
+Keys, sort order, tree topology and groups: bit-exact. Moments: 1e-12
+relative (FP64), b_max 2e-6 relative in the FP32 form. Lists: equal as sets
+except where a test lies within 1e-6 relative of its threshold. Forces: FP64
+form within 1e-12 of the sum of term magnitudes; FP32 form within 1e-5
+relative at the 99th percentile.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1406_6158_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+LIST_BAND = 1e-6
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1406_6158_gb300 import build, hybrid
+    build.build()
+    hybrid.load()
+    return hybrid
+
+
+def oparams(P):
+    return oracle.Params(G=P.G, eps=P.eps, theta=P.theta, R1=P.R1, R2=P.R2, dt_soft=P.dt_soft, a_err=P.a_err,
+                         n_hard=P.n_hard, n_leaf=P.n_leaf, n_crit=P.n_crit, mac=P.mac)
+
+
+def gpu_tree(H, st, P):
+    ctx = H.Context(P)
+    s = H.System(st, precision=P.precision)
+    ctx.hybrid_build_tree(s)
+    torch.cuda.synchronize()
+    return ctx, s, ctx.tree(s.n)
+
+
+def plummer_params(n, prec, **kw):
+    eps = kw.pop("eps", 1.0 / 64)
+    d = dict(eps=eps, theta=0.5, R1=4 * eps, R2=8 * eps, precision=prec)
+    d.update(kw)
+    from paper_1406_6158_gb300 import hybrid
+    return hybrid.Params(**d)
+
+
+CASES = [
+    ("plummer4096", lambda: ics.plummer(4096, 0), {}),
+    ("plummer10007_ragged", lambda: ics.plummer(10007, 3), dict(n_crit=32, n_leaf=8)),
+    ("hernquist20000", lambda: ics.hernquist(20000, 2), dict(theta=0.4, eps=1 / 512)),
+    ("leaf1_capacity", lambda: ics.plummer(6000, 5), dict(n_leaf=1, n_crit=16)),
+]
+
+
+def coincident_state():
+    n = 300
+    st = ics.plummer(n, 7)
+    for k in ("x", "y", "z"):
+        st[k][:100] = 0.125                      # 100 particles on one point
+    st["x"][100:130] = st["x"][100]              # 30 on a line
+    return st
+
+
+def check_tree(T, G, prec):
+    n = T.n
+    assert np.array_equal(G["key"], T.key)
+    assert len(G["level"]) == T.nn
+    for f in ("level", "first", "count", "child", "nchild", "parent"):
+        assert np.array_equal(G[f], getattr(T, f)), f
+    assert np.array_equal(G["gnode"], T.gnode)
+    assert np.array_equal(G["glo"], T.glo) and np.array_equal(G["ghi"], T.ghi)
+    mo, gm = T.moments, G["moments"]
+    scale = np.abs(np.stack([mo["cx"], mo["cy"], mo["cz"]], 1)).max(1) + mo["side"]
+    assert np.all(np.abs(gm[:, 0] - mo["M"]) <= 1e-12 * mo["M"] + 1e-300)
+    for k, f in ((1, "cx"), (2, "cy"), (3, "cz")):
+        assert np.all(np.abs(gm[:, k] - mo[f]) <= 1e-12 * scale), f
+    assert np.array_equal(gm[:, 7], mo["side"])
+    for k, f in ((8, "ox"), (9, "oy"), (10, "oz")):
+        assert np.array_equal(gm[:, k], mo[f]), f
+    assert np.all(np.abs(gm[:, 5] - mo["B2"]) <= 1e-12 * (mo["B2"] + mo["M"] * mo["side"] ** 2))
+    assert np.all(np.abs(gm[:, 6] - mo["delta"]) <= 1e-12 * scale)
+    # FP32 form: b_max from hi/lo differences, good to ~1e-7 relative plus a few lo-part ulps (~L 2^-44)
+    tol, floor = (1e-12, 1e-12 * scale) if prec == 0 else (2e-6, 1e-11 * T.L)
+    assert np.all(np.abs(gm[:, 4] - mo["bmax"]) <= tol * mo["bmax"] + floor)
+    fin = np.isfinite(mo["rb"])
+    assert np.array_equal(np.isfinite(gm[:, 11]), fin)
+    assert np.all(np.abs(gm[fin, 11] - mo["rb"][fin]) <= (1e-12 if prec == 0 else 2e-6) * mo["rb"][fin])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,mk,kw", CASES, ids=[c[0] for c in CASES])
+def test_tree_bit_exact(H, name, mk, kw, prec):
+    st = mk()
+    P = plummer_params(len(st["x"]), prec, **kw)
+    ctx, s, G = gpu_tree(H, st, P)
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], oparams(P))
+    out = s.numpy()
+    assert np.array_equal(out["id"], T.perm)                       # sort order, ties by input order
+    assert np.array_equal(out["x"], T.x) and np.array_equal(out["m"], T.m)
+    assert np.array_equal(ctx.hybrid_get_perm(T.n).cpu().numpy(), T.perm)
+    check_tree(T, G, prec)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 33])
+def test_tiny_and_coincident(H, n):
+    st = ics.plummer(max(n, 2), 9)
+    st = {k: v[:n].copy() for k, v in st.items()}
+    P = plummer_params(n, 1, n_leaf=1, n_crit=2)
+    ctx, s, G = gpu_tree(H, st, P)
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], oparams(P))
+    assert np.array_equal(s.numpy()["id"], T.perm)
+    check_tree(T, G, 1)
+    st = coincident_state()
+    P = plummer_params(len(st["x"]), 0, n_leaf=4, n_crit=8)
+    ctx, s, G = gpu_tree(H, st, P)
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], oparams(P))
+    assert np.array_equal(s.numpy()["id"], T.perm)
+    check_tree(T, G, 0)
+    assert T.level.max() == 21
+
+
+def ancestors(T, c):
+    out = []
+    while c >= 0:
+        out.append(c)
+        c = T.parent[c]
+    return out
+
+
+def leaf_of(T):
+    lf = np.zeros(T.n, dtype=np.int64)
+    for c in np.where(T.nchild == 0)[0]:
+        lf[T.first[c]:T.first[c] + T.count[c]] = c
+    return lf
+
+
+def near_threshold(T, g, c, hard):
+    mo = T.moments
+    p = np.array([mo["cx"][c], mo["cy"][c], mo["cz"][c]])
+    gap = np.maximum(np.maximum(T.glo[g] - p, 0.0), p - T.ghi[g])
+    d = np.sqrt(np.sum(gap * gap))
+    hr = T.params.R2 + mo["bmax"][c]
+    thr = hr if hard else max(mo["rb"][c], hr)
+    return np.isfinite(thr) and abs(d - thr) <= LIST_BAND * thr
+
+
+def lists_match(T, gl, ol):
+    lf = leaf_of(T)
+    flips = 0
+    for g, (a, b) in enumerate(zip(gl, ol)):
+        for k in range(3):
+            A, B = set(a[k].tolist()), set(b[k].tolist())
+            if A == B:
+                continue
+            for e in A ^ B:
+                node = e if k == 0 else lf[e]
+                ok = any(near_threshold(T, g, c, k == 2) for c in ancestors(T, node))
+                assert ok, "group %d list %d entry %d differs away from a threshold" % (g, k, e)
+                flips += 1
+    return flips
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,mk,kw", CASES[:3], ids=[c[0] for c in CASES[:3]])
+def test_lists_and_forces(H, name, mk, kw, prec):
+    st = mk()
+    P = plummer_params(len(st["x"]), prec, **kw)
+    ctx = H.Context(P)
+    s = H.System(st, precision=prec)
+    ctx.hybrid_build_tree(s)
+    ctx.hybrid_hard_force(s)
+    ctx.hybrid_soft_force(s)              # the last walk holds soft lists
+    torch.cuda.synchronize()
+    out = s.numpy()
+    T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
+    assert np.array_equal(T.perm, np.arange(T.n))
+    gl = ctx.lists(T.ng)
+    ol = T.walk(mode=1)
+    flips = lists_match(T, gl, ol)
+    if prec == 0:
+        assert flips == 0
+    a_s, a_h, sc_s, sc_h = T.forces()
+    g_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+    g_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+    if prec == 0:
+        # a pair at r = R2 to the last bit has K ~ 1e-90 on one side and exactly 0 on the other
+        floor = 1e-24 * np.max(sc_s)
+        assert np.all(np.abs(g_s - a_s) <= 1e-12 * sc_s[:, None] + floor)
+        assert np.all(np.abs(g_h - a_h) <= 1e-12 * sc_h[:, None] + floor)
+    else:
+        es = np.linalg.norm(g_s - a_s, axis=1) / np.linalg.norm(a_s, axis=1)
+        assert np.percentile(es, 99) <= 1e-5, np.percentile(es, 99)
+        nz = np.linalg.norm(a_h, axis=1) > 0
+        eh = np.linalg.norm(g_h - a_h, axis=1)[nz] / np.linalg.norm(a_h, axis=1)[nz]
+        assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
+        assert np.all(np.linalg.norm(g_h, axis=1)[~nz] == 0.0)
+    si, hi = ctx.hybrid_interactions()
+    os_, oh = T.interactions(mode=3)
+    assert si == os_ or prec == 1
+    assert abs(si - os_) <= 1e-3 * os_
+
+
+def test_hard_lists_and_theta_zero(H):
+    st = ics.plummer(3000, 4)
+    for prec in (0, 1):
+        P = plummer_params(3000, prec, theta=0.0)
+        ctx = H.Context(P)
+        s = H.System(st, precision=prec)
+        ctx.hybrid_build_tree(s)
+        ctx.hybrid_soft_force(s)
+        ctx.hybrid_hard_force(s)              # the last walk holds hard lists
+        out = s.numpy()
+        T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
+        gl = ctx.lists(T.ng)
+        ol = T.walk(mode=2)
+        assert lists_match(T, gl, ol) == 0 or prec == 1
+        # theta = 0: soft + hard equals direct summation
+        full, sc = oracle.direct(T.x, T.y, T.z, T.m, eps=P.eps)
+        g = (np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64) +
+             np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64))
+        if prec == 0:
+            assert np.all(np.abs(g - full) <= 1e-12 * sc[:, None])
+        else:
+            e = np.linalg.norm(g - full, axis=1) / np.linalg.norm(full, axis=1)
+            assert np.percentile(e, 99) <= 1e-5
+
+
+def test_c1_trajectory_fp64(H):
+    # Plummer N = 4096 seed 0, eps 1/64, theta 0.5, R1 = 4 eps, R2 = 8 eps, dt 1/128, n = 4, 16 steps, FP64
+    st = ics.plummer(4096, 0)
+    st["id"] = np.arange(4096, dtype=np.int64)
+    P = plummer_params(4096, 0, dt_soft=1 / 128, n_hard=4)
+    ctx = H.Context(P)
+    s = H.System(st, precision=0)
+    ctx.hybrid_step(s, 16)
+    out = s.numpy()
+    ost = {k: np.array(v, copy=True) for k, v in st.items()}
+    a_s, a_h = oracle.hybrid_steps(ost, oparams(P), 16)
+    assert np.array_equal(out["id"], ost["id"])
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        assert np.max(np.abs(out[k] - ost[k])) <= 1e-9, k
+    assert np.allclose(np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1), a_s, rtol=0, atol=1e-9)
+
+
+def test_step_fp32_close_to_oracle(H):
+    st = ics.plummer(2048, 8)
+    st["id"] = np.arange(2048, dtype=np.int64)
+    P = plummer_params(2048, 1, dt_soft=1 / 128, n_hard=4)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_step(s, 2)
+    out = s.numpy()
+    ost = {k: np.array(v, copy=True) for k, v in st.items()}
+    oracle.hybrid_steps(ost, oparams(P), 2)
+    o = np.argsort(out["id"])
+    q = np.argsort(ost["id"])
+    for k in ("x", "y", "z"):
+        assert np.max(np.abs(out[k][o] - ost[k][q])) <= 1e-8
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_equals_alone(H, prec):
+    sizes = [1000, 5003, 2500]
+    states = [ics.plummer(n, 20 + k) for k, n in enumerate(sizes)]
+    P = plummer_params(1000, prec, n_hard=2)
+    per = [H.Params(**{**P.__dict__, "eps": 1 / (4 * n ** (1 / 3)), "R1": 4 / (4 * n ** (1 / 3)),
+                       "R2": 8 / (4 * n ** (1 / 3))}) for n in sizes]
+    ctx = H.Context(P)
+    alone = []
+    for st, p in zip(states, per):
+        s = H.System(st, precision=prec, params=p)
+        ctx.hybrid_step(s, 2)
+        alone.append(s.numpy())
+    sysb = [H.System(st, precision=prec, params=p) for st, p in zip(states, per)]
+    ctx.hybrid_step_batched(sysb, 2)
+    for a, s in zip(alone, sysb):
+        b = s.numpy()
+        for k in ("x", "y", "z", "vx", "vy", "vz", "ax_s", "ax_h", "id"):
+            assert np.array_equal(a[k], b[k]), k
+
+
+def test_kick_drift_calls(H):
+    st = ics.plummer(1000, 30)
+    P = plummer_params(1000, 0)
+    ctx = H.Context(P)
+    s = H.System(st, precision=0)
+    s.t["ax_s"].fill_(0.5)
+    s.t["ay_s"].fill_(-0.25)
+    s.t["az_s"].fill_(2.0)
+    ctx.hybrid_kick(s, 0, 0.125)
+    ctx.hybrid_drift(s, 0.0625)
+    out = s.numpy()
+    vx = st["vx"] + 0.125 * 0.5
+    assert np.array_equal(out["vx"], vx)
+    assert np.array_equal(out["x"], st["x"] + 0.0625 * vx)
+
+
+def test_c2_full_size_sampled(H):
+    # Plummer N = 2^17 seed 1, eps 1/128, theta 0.5, R1 = 4 eps, R2 = 8 eps, FP32 pairs (the benchmark workload)
+    n = 1 << 17
+    st = ics.plummer(n, 1)
+    P = plummer_params(n, 1, eps=1 / 128)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_build_tree(s)
+    ctx.hybrid_soft_force(s)
+    ctx.hybrid_hard_force(s)
+    out = s.numpy()
+    T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
+    assert np.array_equal(T.perm, np.arange(n))
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(T.ng, 300, replace=False))
+    a_s, a_h, _, _ = T.forces(groups=sel)
+    mask = ~np.isnan(a_s[:, 0])
+    g_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)[mask]
+    g_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)[mask]
+    es = np.linalg.norm(g_s - a_s[mask], axis=1) / np.linalg.norm(a_s[mask], axis=1)
+    assert np.percentile(es, 99) <= 1e-5
+    nz = np.linalg.norm(a_h[mask], axis=1) > 0
+    eh = np.linalg.norm(g_h - a_h[mask], axis=1)[nz] / np.linalg.norm(a_h[mask], axis=1)[nz]
+    assert np.percentile(eh, 99) <= 1e-5
