@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the hybrid tree force path on GB300.
+
+One step = one soft step dt_s of the hybrid scheme (n_hard hard sub-steps,
+each with a tree rebuild and the hard force, plus the soft force at the last
+one) for one Plummer sphere of N = 2^17 particles (seed 1, eps = 1/128,
+theta = 0.5, R1 = 4 eps, R2 = 8 eps, dt_s = 1/128, n_hard = 4), FP32 pair
+kernels on FP64 state. Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+--gpus N > 1 runs N independent replicas (torchrun, one rank per GPU); the
+path has no exchange step, so there is no collective on the data path.
+--impl reference times the CPU FP64 oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 1 << 17
+METRIC = "particle-steps/s"
+FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul, 3 fma (by convention 20)
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload(n):
+    eps = 1.0 / 128
+    return dict(n=n, seed=1, eps=eps, theta=0.5, R1=4 * eps, R2=8 * eps, dt_soft=1.0 / 128, n_hard=4,
+                n_leaf=16, n_crit=64)
+
+
+def workload_name(w):
+    return ("Plummer sphere N=%d seed %d, eps=1/128, theta=0.5, R1=4eps, R2=8eps, dt_s=1/128, n_hard=4; "
+            "FP32 pair kernels on group-relative coordinates, FP64 state" % (w["n"], w["seed"]))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def fp32_peak_tflops(nsm, sm_mhz):
+    # 128 FP32 lanes per SM, 2 flops per FMA
+    return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        out.update(sm_mhz=sm[len(sm) // 2] if sm else None, sm_max_mhz=max(mx) if mx else None, reasons=reasons,
+                   samples=len(rows))
+        return out
+
+
+def force_error_rms(state, a_s, a_h, eps, nsample=512, seed=0):
+    """rms over sampled sinks of |a_gpu - a_direct| / |a_direct| (direct FP64 summation, CPU)."""
+    import numpy as np
+    import oracle
+    n = len(state["x"])
+    rng = np.random.default_rng(seed)
+    sink = np.sort(rng.choice(n, min(nsample, n), replace=False))
+    full, _ = oracle.direct(state["x"], state["y"], state["z"], state["m"], eps=eps, sinks=sink)
+    a = (a_s + a_h)[sink]
+    e = np.linalg.norm(a - full, axis=1) / np.linalg.norm(full, axis=1)
+    return float(np.sqrt(np.mean(e * e)))
+
+
+def cpu_baseline(w, max_seconds=20.0):
+    """The oracle as it stands, on this host's cores: whole hybrid steps of the same workload."""
+    import numpy as np
+    import oracle
+    from paper_1406_6158_gb300 import ics
+    st = ics.plummer(w["n"], w["seed"])
+    p = oracle.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
+                      n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"])
+    a_s, a_h = oracle.forces(st, p)
+    steps, t = 0, 0.0
+    while t < max_seconds and steps < 64:
+        t0 = time.perf_counter()
+        a_s, a_h = oracle.hybrid_steps(st, p, 1, a_s, a_h)
+        t += time.perf_counter() - t0
+        steps += 1
+    return {"value": w["n"] * steps / t, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d whole soft step(s) of the same workload (N=%d), FP64, OpenMP over sink groups" %
+                      (steps, w["n"]), "seconds": t}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import numpy as np
+    from paper_1406_6158_gb300 import ics
+    st = ics.plummer(w["n"], w["seed"])
+    p = oracle.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
+                      n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"])
+    a_s, a_h = oracle.forces(st, p)
+    for _ in range(args.warmup):
+        a_s, a_h = oracle.hybrid_steps(st, p, 1, a_s, a_h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        a_s, a_h = oracle.hybrid_steps(st, p, 1, a_s, a_h)
+    t = time.perf_counter() - t0
+    v = w["n"] * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "N": w["n"], "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "%d whole soft steps of the workload after %d warm-up steps" %
+                                   (args.steps, args.warmup)},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--traffic-bytes", type=float, default=None,
+                    help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
+    args = ap.parse_args()
+    w = workload(args.n)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    args.warmup = max(args.warmup, 3)
+
+    import numpy as np
+    import torch
+    from paper_1406_6158_gb300 import build as cuda_build
+    from paper_1406_6158_gb300 import hybrid, ics
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or not os.path.exists(hybrid.LIB_PATH):
+        cuda_build.build()
+    if dist:
+        dist.barrier()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    P = hybrid.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
+                      n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"], precision=1)
+    stream = torch.cuda.current_stream()
+    ctx = hybrid.Context(P, stream)
+    st = ics.plummer(w["n"], w["seed"])
+    s = hybrid.System(st, precision=1)
+    ctx.hybrid_step(s, 0)                      # forces at the initial positions
+    for _ in range(args.warmup):
+        ctx.hybrid_step(s, 1)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # ---- device-timed region: inputs resident in HBM, L2 flushed before every step ----
+    clocks = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.hybrid_profile(True)
+    ctx.hybrid_profile_read(0, reset=True)
+    launches0 = ctx.hybrid_launch_count()
+    inter_soft = inter_hard = 0
+    barrier()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.hybrid_step(s, 1)
+        ev[k][1].record(stream)
+        si, hi = ctx.hybrid_interactions()     # the last soft/hard evaluation of this step
+        inter_soft += si
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.hybrid_launch_count() - launches0
+    t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    soft_ms, soft_n = ctx.hybrid_profile_read(0)
+    hard_ms, hard_n = ctx.hybrid_profile_read(1)
+    walk_ms, walk_n = ctx.hybrid_profile_read(2)
+    tree_ms, tree_n = ctx.hybrid_profile_read(3)
+    integ_ms, integ_n = ctx.hybrid_profile_read(4, reset=True)
+    ctx.hybrid_profile(False)
+    if dist:
+        t = torch.tensor([t_steps], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_steps = float(t.item())
+    value = ws * w["n"] * args.steps / t_steps
+
+    # ---- end to end through the C-ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        keys = ["x", "y", "z", "vx", "vy", "vz", "m", "ax_s", "ay_s", "az_s", "ax_h", "ay_h", "az_h", "id"]
+        host = {k: s.t[k].detach().cpu().pin_memory() for k in keys}
+        h2d = sum(host[k].numel() * host[k].element_size() for k in keys)
+        ke = max(3, args.steps // 2)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            for k in keys:
+                s.t[k].copy_(host[k], non_blocking=True)
+            ctx.hybrid_step(s, 1)
+            for k in keys:
+                host[k].copy_(s.t[k], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+        e1.record(stream)
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": ws * w["n"] * ke / te, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+               "steps": ke}
+
+    # ---- roofline of the dominant kernel (soft pair, FP32 CUDA-core bound) ----
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    soft_avg_s = (soft_ms / 1e3) / max(soft_n, 1)
+    per_launch_flops = FLOPS_PER_INTERACTION * inter_soft / max(args.steps, 1)
+    achieved = per_launch_flops / soft_avg_s / 1e12 if soft_avg_s > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": args.traffic_bytes,
+                "kernel": "k_pair_f32 (soft)",
+                "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
+                             (props.multi_processor_count, sm_max)}
+
+    line = None
+    if rank == 0:
+        out = s.numpy()
+        a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+        a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+        ferr = force_error_rms(out, a_s, a_h, w["eps"])
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            cpu = cpu_baseline(w)
+        step_ms = 1e3 * t_steps / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(w), "N": w["n"], "parallelism": "replicas x%d" % ws,
+                       "l2": "flushed (256 MiB write) before every timed step", "state": "f64"},
+            "interactions_per_s": ws * inter_soft / t_steps,
+            "soft_interactions_per_step": inter_soft / args.steps,
+            "force_err_rms_vs_direct": ferr,
+            "kernel_ms_per_step": {"soft_pair": soft_ms / args.steps, "hard_pair": hard_ms / args.steps,
+                                   "walk": walk_ms / args.steps, "tree_build": tree_ms / args.steps,
+                                   "kick_drift": integ_ms / args.steps},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -114,7 +114,8 @@ struct hybrid_ctx {
     hy::Buf off_dev, sp_dev, chunks_dev, boxmin, boxmax, box, sysroot;
     hy::Buf status;
     // tree
-    hy::Buf lvl, nfirst, ncount, nchild, nnch, nparent, nlevel, ndone, nchtmp, leafof;
+    hy::Buf lvl, nfirst, ncount, nchild, nnch, nparent, nlevel, ndone, leafof;
+    hy::Buf pc, pD, pn, rec, rb2d, rd2b, rhist;     // topology build scratch
     hy::Buf nM, ncx, ncy, ncz, nB2, nbmax;     // FP64 moments
     hy::Buf nA, nB, ncrit, ntopo;              // FP32 walk/pair node data
     hy::Buf nD, nrb, nhr;                      // FP64 walk/pair node data (precision 0)

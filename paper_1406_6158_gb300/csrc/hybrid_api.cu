@@ -138,8 +138,11 @@ bool alloc_nodes(hybrid_ctx *c, int64_t cap)
 {
     const size_t n = (size_t)cap;
     bool ok = true;
-    for (Buf *b : {&c->nfirst, &c->ncount, &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->nchtmp})
+    for (Buf *b : {&c->nfirst, &c->ncount, &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->rb2d,
+                   &c->rd2b})
         ok = ok && ensure(c, *b, n * 4);
+    ok = ok && ensure(c, c->rec, n * 8);
+    ok = ok && ensure(c, c->rhist, (size_t)(LEVELS + 1) * ((n + RS_TILE - 1) / RS_TILE) * 4);
     for (Buf *b : {&c->nM, &c->ncx, &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nrb, &c->nhr, &c->ndelta, &c->nside})
         ok = ok && ensure(c, *b, n * 8);
     ok = ok && ensure(c, c->norg, n * 24);
@@ -157,8 +160,9 @@ bool reserve(hybrid_ctx *c)
         const size_t n = (size_t)N;
         for (int f = 0; f < 7; ++f) ok = ok && ensure(c, c->x[f], n * 8) && ensure(c, c->xa[f], n * 8);
         for (Buf *b : {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->leafof, &c->gflag, &c->gscan, &c->gnode,
-                       &c->gfirst, &c->gcount, &c->gsys})
+                       &c->gfirst, &c->gcount, &c->gsys, &c->pn})
             ok = ok && ensure(c, *b, n * 4);
+        ok = ok && ensure(c, c->pc, n) && ensure(c, c->pD, n);
         const size_t asz = c->p.precision == 1 ? 4 : 8;
         for (int d = 0; d < 3; ++d) ok = ok && ensure(c, c->acc_s[d], n * asz) && ensure(c, c->acc_h[d], n * asz);
         if (c->p.precision == 1) ok = ok && ensure(c, c->phi, n * 16) && ensure(c, c->plo, n * 16);
@@ -520,7 +524,8 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
     Buf *all[] = {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->phi, &c->plo, &c->pd, &c->keys[0], &c->keys[1],
                   &c->vals[0], &c->vals[1], &c->hist, &c->blocksum, &c->off_dev, &c->sp_dev, &c->chunks_dev,
                   &c->boxmin, &c->boxmax, &c->box, &c->sysroot, &c->status, &c->lvl, &c->nfirst, &c->ncount,
-                  &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->nchtmp, &c->leafof, &c->nM, &c->ncx,
+                  &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->leafof, &c->pc, &c->pD, &c->pn, &c->rec,
+                  &c->rb2d, &c->rd2b, &c->rhist, &c->nM, &c->ncx,
                   &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
                   &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
                   &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,

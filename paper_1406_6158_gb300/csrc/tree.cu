@@ -295,123 +295,255 @@ __global__ void __launch_bounds__(256) k_permute(PermArgs a, const Status *st)
 }
 
 // ---------------------------------------------------------------------------
-// Level-wise split. Nodes are numbered breadth first: level by level, and in
-// a level by system, then key. lvl[l] is the first node of level l.
+// Octree topology from the sorted keys, all levels at once.
+//
+// c(i) = number of leading octal digits keys i-1 and i share (-1 at the first
+// particle of a system): particle i starts a cell at every level l > c(i).
+// The level-l cell around particle p spans positions up to the nearest
+// starts on either side, so its size is known from c in a window of n_leaf
+// positions whenever it is at most n_leaf. The leaf depth D(p) is the first
+// level whose cell holds <= n_leaf particles (21 at most): cells exist down to
+// D(p). Particle i therefore owns the nodes (l, first = i) for
+// c(i) < l <= D(i). These records are written in particle order (a scan
+// gives each particle its slot), then stably sorted by level: the result is
+// the breadth-first order (level, system, key) of the split rule.
 // ---------------------------------------------------------------------------
-__global__ void k_roots(int S, const int64_t *__restrict__ off, uint32_t *nfirst, uint32_t *ncount,
-                        uint32_t *nparent, uint32_t *nlevel, uint32_t *lvl, uint32_t *sysroot, const Status *st)
+__global__ void __launch_bounds__(256) k_prefix_c(int64_t N, const uint64_t *__restrict__ key,
+                                                  const int32_t *__restrict__ psys, int8_t *__restrict__ pc,
+                                                  const Status *st)
 {
     if (st->code) return;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < S) {
-        nfirst[s] = (uint32_t)off[s];
-        ncount[s] = (uint32_t)(off[s + 1] - off[s]);
-        nparent[s] = NONE;
-        nlevel[s] = 0;
-        sysroot[s] = (uint32_t)s;
-    }
-    if (s == 0) {
-        lvl[0] = 0;
-        for (int l = 1; l < LEVELS + 3; ++l) lvl[l] = (uint32_t)S;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        int c;
+        if (i == 0 || psys[i] != psys[i - 1]) {
+            c = -1;
+        } else {
+            const unsigned long long x = key[i - 1] ^ key[i];
+            c = x == 0ull ? LEVELS : (__clzll((long long)x) - 1) / 3;   // keys use bits 0..62
+        }
+        pc[i] = (int8_t)c;
     }
 }
 
-__device__ __forceinline__ uint32_t digit_at(uint64_t key, int lev)
-{
-    return (uint32_t)(key >> (3 * (LEVELS - lev))) & 7u;
-}
+constexpr int LD_T = 256;
 
-// Boundaries of the 8 octants (at level clev) inside the sorted range
-// [f, f + n): b[d] = first index whose digit is >= d. Seven interleaved
-// binary searches.
-__device__ __forceinline__ void octant_bounds(const uint64_t *__restrict__ key, uint32_t f, uint32_t n, int clev,
-                                              uint32_t b[9])
+// Leaf depth D(p) and the number of nodes particle p starts, max(0, D - c).
+__global__ void __launch_bounds__(LD_T) k_leaf_depth(int64_t N, const int8_t *__restrict__ pc, int n_leaf,
+                                                     uint8_t *__restrict__ pD, uint32_t *__restrict__ pn,
+                                                     const Status *st)
 {
-    uint32_t lo[7], hi[7];
-#pragma unroll
-    for (int d = 0; d < 7; ++d) {
-        lo[d] = f;
-        hi[d] = f + n;
-    }
-    for (uint32_t span = n; span > 0; span >>= 1) {
-#pragma unroll
-        for (int d = 0; d < 7; ++d) {
-            if (lo[d] < hi[d]) {
-                const uint32_t mid = lo[d] + ((hi[d] - lo[d]) >> 1);
-                if (digit_at(key[mid], clev) < (uint32_t)(d + 1)) lo[d] = mid + 1;
-                else hi[d] = mid;
+    if (st->code) return;
+    extern __shared__ int8_t sc[];   // LD_T + 2 n_leaf values of c
+    const int win = LD_T + 2 * n_leaf;
+    for (int64_t base = (int64_t)blockIdx.x * LD_T; base < N; base += (int64_t)gridDim.x * LD_T) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < win; k += blockDim.x) {
+            const int64_t j = base - n_leaf + k;
+            sc[k] = (j < 0 || j >= N) ? (int8_t)-1 : pc[j];
+        }
+        __syncthreads();
+        const int64_t p = base + threadIdx.x;
+        if (p < N) {
+            const int w = threadIdx.x + n_leaf;
+            // size of the level-lev cell around p, capped at n_leaf + 1 on each side
+            auto count_at = [&](int lev) {
+                int kl = 0;
+                while (kl <= n_leaf && sc[w - kl] >= lev) ++kl;
+                int kr = 1;
+                while (kr <= n_leaf && sc[w + kr] >= lev) ++kr;
+                return kl + kr;
+            };
+            int D;
+            if (count_at(LEVELS) > n_leaf) {
+                D = LEVELS;
+            } else {
+                int lo = 0, hi = LEVELS;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (count_at(mid) <= n_leaf) hi = mid;
+                    else lo = mid + 1;
+                }
+                D = lo;
             }
+            const int c = sc[w];
+            pD[p] = (uint8_t)D;
+            pn[p] = D > c ? (uint32_t)(D - c) : 0u;
         }
-    }
-    // the loop above runs log2(n)+1 rounds, enough for every search to close
-    b[0] = f;
-#pragma unroll
-    for (int d = 0; d < 7; ++d) b[d + 1] = lo[d];
-    b[8] = f + n;
-}
-
-__global__ void __launch_bounds__(256) k_level_count(int lev, const uint32_t *__restrict__ lvl,
-                                                     const uint32_t *__restrict__ nfirst,
-                                                     const uint32_t *__restrict__ ncount,
-                                                     const uint64_t *__restrict__ key, int n_leaf,
-                                                     uint32_t *__restrict__ nch, int64_t *d_n, const Status *st)
-{
-    if (st->code) return;
-    const uint32_t a = lvl[lev], e = lvl[lev + 1];
-    if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = (int64_t)(e - a);
-    for (uint32_t c = a + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
-        const uint32_t cnt = ncount[c];
-        uint32_t k = 0;
-        if (cnt > (uint32_t)n_leaf && lev < LEVELS) {
-            uint32_t b[9];
-            octant_bounds(key, nfirst[c], cnt, lev + 1, b);
-#pragma unroll
-            for (int d = 0; d < 8; ++d) k += (b[d + 1] > b[d]) ? 1u : 0u;
-        }
-        nch[c - a] = k;
     }
 }
 
-__global__ void __launch_bounds__(256) k_level_emit(int lev, uint32_t *lvl, uint32_t *nfirst, uint32_t *ncount,
-                                                    const uint64_t *__restrict__ key, int n_leaf,
-                                                    const uint32_t *__restrict__ choff, const uint64_t *total,
-                                                    int64_t cap, uint32_t *nchild, uint32_t *nnch, uint32_t *nparent,
-                                                    uint32_t *nlevel, Status *st, int where)
+// records (level << 32 | first) in particle order
+__global__ void __launch_bounds__(256) k_records(int64_t N, const int8_t *__restrict__ pc,
+                                                 const uint8_t *__restrict__ pD, const uint32_t *__restrict__ poff,
+                                                 const uint64_t *__restrict__ total, int64_t cap,
+                                                 unsigned long long *__restrict__ rec, Status *st, int where)
 {
     if (st->code) return;
-    const uint32_t a = lvl[lev], e = lvl[lev + 1];
-    const uint64_t tot = *total;
-    if ((int64_t)e + (int64_t)tot > cap) {
+    if ((int64_t)*total > cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             fail(st, HYBRID_ECAPACITY, where);
-            st->need[0] = 2 * ((int64_t)e + (int64_t)tot);
+            st->need[0] = (int64_t)*total + (int64_t)(*total >> 3) + 1024;
         }
         return;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) lvl[lev + 2] = e + (uint32_t)tot;
-    for (uint32_t c = a + blockIdx.x * blockDim.x + threadIdx.x; c < e; c += gridDim.x * blockDim.x) {
-        const uint32_t cnt = ncount[c];
-        if (cnt > (uint32_t)n_leaf && lev < LEVELS) {
-            uint32_t b[9];
-            octant_bounds(key, nfirst[c], cnt, lev + 1, b);
-            const uint32_t base = e + choff[c - a];
-            uint32_t k = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = pc[i], D = pD[i];
+        uint32_t o = poff[i];
+        for (int l = c + 1; l <= D; ++l) rec[o++] = ((unsigned long long)l << 32) | (unsigned long long)i;
+    }
+}
+
+constexpr int REC_TILE = RS_TILE;   // 4096 records per tile, 8 warps x 32 lanes x 16
+constexpr int NLEV = LEVELS + 1;    // levels 0..21
+
+__global__ void __launch_bounds__(256) k_rec_hist(const unsigned long long *__restrict__ rec,
+                                                  const uint64_t *__restrict__ total, int ntiles,
+                                                  uint32_t *__restrict__ hist, const Status *st)
+{
+    if (st->code) return;
+    __shared__ uint32_t h[NLEV];
+    const uint64_t T = *total;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (threadIdx.x < NLEV) h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint64_t b0 = (uint64_t)t * REC_TILE;
+        for (int k = threadIdx.x; k < REC_TILE; k += blockDim.x)
+            if (b0 + k < T) atomicAdd(&h[(uint32_t)(rec[b0 + k] >> 32)], 1u);
+        __syncthreads();
+        if (threadIdx.x < NLEV) hist[(size_t)threadIdx.x * ntiles + t] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// stable scatter by level; also the level starts lvl[0..23]
+__global__ void __launch_bounds__(256) k_rec_scatter(const unsigned long long *__restrict__ rec,
+                                                     const uint64_t *__restrict__ total, int ntiles,
+                                                     const uint32_t *__restrict__ hoff, uint32_t *__restrict__ bfs2dfs,
+                                                     uint32_t *__restrict__ dfs2bfs, uint32_t *__restrict__ lvl,
+                                                     const Status *st)
+{
+    if (st->code) return;
+    __shared__ uint32_t whist[RS_WARPS][NLEV];
+    __shared__ uint32_t base[NLEV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const uint64_t T = *total;
+    if (blockIdx.x == 0 && threadIdx.x <= NLEV + 1)
+        lvl[threadIdx.x] = threadIdx.x < NLEV ? hoff[(size_t)threadIdx.x * ntiles] : (uint32_t)T;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t b0 = (uint64_t)t * REC_TILE;
+        if (b0 >= T) break;
+        for (int k = threadIdx.x; k < RS_WARPS * NLEV; k += blockDim.x) (&whist[0][0])[k] = 0;
+        if (threadIdx.x < NLEV) base[threadIdx.x] = hoff[(size_t)threadIdx.x * ntiles + t];
+        __syncthreads();
+        uint32_t lv[RS_IPT], r[RS_IPT];
+        const int wbase = w * 32 * RS_IPT;
 #pragma unroll
-            for (int d = 0; d < 8; ++d) {
-                if (b[d + 1] > b[d]) {
-                    const uint32_t q = base + k++;
-                    nfirst[q] = b[d];
-                    ncount[q] = b[d + 1] - b[d];
-                    nparent[q] = c;
-                    nlevel[q] = (uint32_t)(lev + 1);
-                }
-            }
-            nchild[c] = base;
-            nnch[c] = k;
-        } else {
-            nchild[c] = NONE;
-            nnch[c] = 0;
+        for (int it = 0; it < RS_IPT; ++it) {
+            const uint64_t li = b0 + wbase + it * 32 + lane;
+            const bool ok = li < T;
+            const uint32_t d = ok ? (uint32_t)(rec[li] >> 32) : 32u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t before = ok ? whist[w][d] : 0u;
+            __syncwarp();
+            if (ok && (peers & ltmask) == 0u) whist[w][d] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            r[it] = before + (uint32_t)__popc(peers & ltmask);
+            lv[it] = d;
         }
+        __syncthreads();
+        if (threadIdx.x < NLEV) {
+            uint32_t run = 0;
+            for (int ww = 0; ww < RS_WARPS; ++ww) {
+                const uint32_t cnt = whist[ww][threadIdx.x];
+                whist[ww][threadIdx.x] = run;
+                run += cnt;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < RS_IPT; ++it) {
+            const uint64_t li = b0 + wbase + it * 32 + lane;
+            if (li < T) {
+                const uint32_t dst = base[lv[it]] + whist[w][lv[it]] + r[it];
+                bfs2dfs[dst] = (uint32_t)li;
+                dfs2bfs[li] = dst;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// per node: level, first, count (end of the key-prefix run, exponential then
+// binary search), first child, parent of the roots, system roots
+__global__ void __launch_bounds__(256) k_nodes_a(const uint64_t *__restrict__ total,
+                                                 const uint32_t *__restrict__ bfs2dfs,
+                                                 const uint32_t *__restrict__ dfs2bfs,
+                                                 const unsigned long long *__restrict__ rec,
+                                                 const uint8_t *__restrict__ pD, const uint64_t *__restrict__ key,
+                                                 const int32_t *__restrict__ psys, const int64_t *__restrict__ off,
+                                                 uint32_t *nfirst, uint32_t *ncount, uint32_t *nlevel, uint32_t *nchild,
+                                                 uint32_t *nparent, uint32_t *sysroot, const Status *st)
+{
+    if (st->code) return;
+    const uint64_t T = *total;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < T; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t r = bfs2dfs[b];
+        const unsigned long long R = rec[r];
+        const int lev = (int)(R >> 32);
+        const uint32_t f = (uint32_t)R;
+        const int s = psys[f];
+        const uint32_t send = (uint32_t)off[s + 1];
+        uint32_t end;
+        if (lev == 0) {
+            end = send;
+            nparent[b] = NONE;
+            sysroot[s] = (uint32_t)b;
+        } else {
+            const int sh = 3 * (LEVELS - lev);
+            const uint64_t pre = key[f] >> sh;
+            uint32_t step = 1, lo = f;   // key[lo] has the prefix
+            while (f + step < send && (key[f + step] >> sh) == pre) {
+                lo = f + step;
+                step <<= 1;
+            }
+            uint32_t hi = min(f + step, send);   // first index known not to have it (or the end)
+            while (hi - lo > 1) {
+                const uint32_t mid = lo + ((hi - lo) >> 1);
+                if ((key[mid] >> sh) == pre) lo = mid;
+                else hi = mid;
+            }
+            end = hi;
+        }
+        nfirst[b] = f;
+        ncount[b] = end - f;
+        nlevel[b] = (uint32_t)lev;
+        nchild[b] = (lev < (int)pD[f]) ? dfs2bfs[r + 1] : NONE;
+    }
+}
+
+// children: the level l+1 nodes that start inside the parent's range
+__global__ void __launch_bounds__(256) k_nodes_b(const uint64_t *__restrict__ total, const uint32_t *__restrict__ lvl,
+                                                 const uint32_t *__restrict__ nfirst,
+                                                 const uint32_t *__restrict__ ncount,
+                                                 const uint32_t *__restrict__ nlevel,
+                                                 const uint32_t *__restrict__ nchild, uint32_t *nnch,
+                                                 uint32_t *nparent, const Status *st)
+{
+    if (st->code) return;
+    const uint64_t T = *total;
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < T; b += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t ch = nchild[b];
+        uint32_t k = 0;
+        if (ch != NONE) {
+            const uint32_t end = nfirst[b] + ncount[b];
+            const uint32_t lend = lvl[nlevel[b] + 2];
+            while (k < 8 && ch + k < lend && nfirst[ch + k] < end) {
+                nparent[ch + k] = (uint32_t)b;
+                ++k;
+            }
+        }
+        nnch[b] = k;
     }
 }
 
@@ -431,6 +563,11 @@ struct MomArgs {
     float4 *nA, *nB;
     uint32_t *done, *leafof;
 };
+
+__device__ __forceinline__ uint32_t digit_at(uint64_t key, int lev)
+{
+    return (uint32_t)(key >> (3 * (LEVELS - lev))) & 7u;
+}
 
 __device__ __forceinline__ void cell_geom(const SysBox &b, uint64_t key, uint32_t lev, double o[3], double *side)
 {
@@ -836,25 +973,35 @@ void launch_keys_sort_permute(hybrid_ctx *c)
 bool launch_build_levels(hybrid_ctx *c)
 {
     Status *st = status_dev(c);
-    uint32_t *lvl = (uint32_t *)c->lvl.p;
-    k_roots<<<(c->S + 127) / 128, 128, 0, c->st>>>(c->S, (const int64_t *)c->off_dev.p, (uint32_t *)c->nfirst.p,
-                                                   (uint32_t *)c->ncount.p, (uint32_t *)c->nparent.p,
-                                                   (uint32_t *)c->nlevel.p, lvl, (uint32_t *)c->sysroot.p, st);
-    c->launches++;
-    int64_t *d_n = (int64_t *)((char *)c->lvl.p + 64 * sizeof(uint32_t));
-    uint64_t *d_tot = (uint64_t *)((char *)c->lvl.p + 64 * sizeof(uint32_t) + 64);
+    const int64_t N = c->N;
+    const int gridN = grid_for(c, N, 256, 8);
+    int8_t *pc = (int8_t *)c->pc.p;
+    uint8_t *pD = (uint8_t *)c->pD.p;
+    uint32_t *pn = (uint32_t *)c->pn.p;
     const uint64_t *keys = (const uint64_t *)c->keys[0].p;
-    const int grid = grid_for(c, c->capNodes, 256, 4);
-    for (int lev = 0; lev <= LEVELS; ++lev) {
-        k_level_count<<<grid, 256, 0, c->st>>>(lev, lvl, (const uint32_t *)c->nfirst.p, (const uint32_t *)c->ncount.p,
-                                                keys, c->p.n_leaf, (uint32_t *)c->nchtmp.p, d_n, st);
-        scan_u32(c, (uint32_t *)c->nchtmp.p, 0, d_n, c->capNodes, d_tot);
-        k_level_emit<<<grid, 256, 0, c->st>>>(lev, lvl, (uint32_t *)c->nfirst.p, (uint32_t *)c->ncount.p, keys,
-                                               c->p.n_leaf, (const uint32_t *)c->nchtmp.p, d_tot, c->capNodes,
-                                               (uint32_t *)c->nchild.p, (uint32_t *)c->nnch.p, (uint32_t *)c->nparent.p,
-                                               (uint32_t *)c->nlevel.p, st, c->op);
-        c->launches += 2;
-    }
+    uint64_t *d_tot = (uint64_t *)((char *)c->lvl.p + 256);
+    k_prefix_c<<<gridN, 256, 0, c->st>>>(N, keys, (const int32_t *)c->psys.p, pc, st);
+    const size_t shm = (size_t)(LD_T + 2 * c->p.n_leaf);
+    k_leaf_depth<<<grid_for(c, N, LD_T, 8), LD_T, shm, c->st>>>(N, pc, c->p.n_leaf, pD, pn, st);
+    scan_u32(c, pn, N, nullptr, N, d_tot);
+    unsigned long long *rec = (unsigned long long *)c->rec.p;
+    k_records<<<gridN, 256, 0, c->st>>>(N, pc, pD, pn, d_tot, c->capNodes, rec, st, c->op);
+    const int ntiles = (int)((c->capNodes + REC_TILE - 1) / REC_TILE);
+    uint32_t *rh = (uint32_t *)c->rhist.p;
+    k_rec_hist<<<std::min(ntiles, c->nsm * 4), 256, 0, c->st>>>(rec, d_tot, ntiles, rh, st);
+    scan_u32(c, rh, (int64_t)NLEV * ntiles, nullptr, (int64_t)NLEV * ntiles, nullptr);
+    uint32_t *b2d = (uint32_t *)c->rb2d.p, *d2b = (uint32_t *)c->rd2b.p;
+    uint32_t *lvl = (uint32_t *)c->lvl.p;
+    k_rec_scatter<<<std::min(ntiles, c->nsm * 4), 256, 0, c->st>>>(rec, d_tot, ntiles, rh, b2d, d2b, lvl, st);
+    const int gridT = grid_for(c, c->capNodes, 256, 8);
+    k_nodes_a<<<gridT, 256, 0, c->st>>>(d_tot, b2d, d2b, rec, pD, keys, (const int32_t *)c->psys.p,
+                                        (const int64_t *)c->off_dev.p, (uint32_t *)c->nfirst.p, (uint32_t *)c->ncount.p,
+                                        (uint32_t *)c->nlevel.p, (uint32_t *)c->nchild.p, (uint32_t *)c->nparent.p,
+                                        (uint32_t *)c->sysroot.p, st);
+    k_nodes_b<<<gridT, 256, 0, c->st>>>(d_tot, lvl, (const uint32_t *)c->nfirst.p, (const uint32_t *)c->ncount.p,
+                                        (const uint32_t *)c->nlevel.p, (const uint32_t *)c->nchild.p,
+                                        (uint32_t *)c->nnch.p, (uint32_t *)c->nparent.p, st);
+    c->launches += 8;
     return true;
 }
 
