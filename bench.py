@@ -233,7 +233,7 @@ def main():
     ctx.hybrid_profile(True)
     ctx.hybrid_profile_read(0, reset=True)
     launches0 = ctx.hybrid_launch_count()
-    inter_soft = inter_hard = 0
+    inter_far = inter_near = 0
     barrier()
     clocks.start()
     for k in range(args.steps):
@@ -241,8 +241,9 @@ def main():
         ev[k][0].record(stream)
         ctx.hybrid_step(s, 1)
         ev[k][1].record(stream)
-        si, hi = ctx.hybrid_interactions()     # the last soft/hard evaluation of this step
-        inter_soft += si
+        fi, ni = ctx.hybrid_interactions()     # pairs of the far and near kernels of the step's soft evaluation
+        inter_far += fi
+        inter_near += ni
     barrier()
     clk = clocks.stop()
     launches = ctx.hybrid_launch_count() - launches0
@@ -292,11 +293,11 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     soft_avg_s = (soft_ms / 1e3) / max(soft_n, 1)
-    per_launch_flops = FLOPS_PER_INTERACTION * inter_soft / max(args.steps, 1)
+    per_launch_flops = FLOPS_PER_INTERACTION * inter_far / max(args.steps, 1)
     achieved = per_launch_flops / soft_avg_s / 1e12 if soft_avg_s > 0 else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": args.traffic_bytes,
-                "kernel": "k_pair_f32 (soft)",
+                "kernel": "k_pair_f32 far (cells + far particles, soft force)",
                 "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
                              (props.multi_processor_count, sm_max)}
 
@@ -316,10 +317,12 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(w), "N": w["n"], "parallelism": "replicas x%d" % ws,
                        "l2": "flushed (256 MiB write) before every timed step", "state": "f64"},
-            "interactions_per_s": ws * inter_soft / t_steps,
-            "soft_interactions_per_step": inter_soft / args.steps,
+            # soft force: far + near pairs once per step; hard force: near pairs at each of the n_hard sub-steps
+            "interactions_per_s": ws * (inter_far + w["n_hard"] * inter_near) / t_steps,
+            "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
+            "hard_interactions_per_substep": inter_near / args.steps,
             "force_err_rms_vs_direct": ferr,
-            "kernel_ms_per_step": {"soft_pair": soft_ms / args.steps, "hard_pair": hard_ms / args.steps,
+            "kernel_ms_per_step": {"far_pair": soft_ms / args.steps, "near_pair": hard_ms / args.steps,
                                    "walk": walk_ms / args.steps, "tree_build": tree_ms / args.steps,
                                    "kick_drift": integ_ms / args.steps},
             "roofline": roofline,

@@ -170,9 +170,12 @@ hybrid_status hybrid_tree_copy(hybrid_ctx *ctx, uint64_t *keys, int32_t *level, 
  * entries = NULL to get the counts only. */
 hybrid_status hybrid_lists_copy(hybrid_ctx *ctx, int64_t *counts, int64_t *entries, int64_t cap_entries);
 
-/* Sink-source pairs evaluated by the soft and hard pair kernels of the last
- * force evaluation (sum over groups of |group| x list length). */
-hybrid_status hybrid_interactions(hybrid_ctx *ctx, int64_t *soft, int64_t *hard);
+/* Sink-source pairs (sum over groups of |group| x list length) of the last
+ * force evaluation: far = pairs with K = 0 for certain (taken cells and far
+ * particles, soft force only); near = near-particle pairs (soft force with
+ * weight 1 - K and hard force with weight K). The soft force sums far + near
+ * pairs, the hard force the near pairs. */
+hybrid_status hybrid_interactions(hybrid_ctx *ctx, int64_t *far, int64_t *near);
 
 /* Profiling: when enabled, the pair kernels are bracketed by CUDA events on
  * the context stream. hybrid_profile_read synchronises and returns, per

@@ -15,9 +15,9 @@ namespace hy {
 
 constexpr int LEVELS = 21;                 // 3 x 21 = 63 Morton key bits
 constexpr uint32_t NONE = 0xFFFFFFFFu;
-constexpr int RS_WARPS = 8;                // radix sort: 8 warps x 32 lanes x 16 items
-constexpr int RS_IPT = 16;
-constexpr int RS_TILE = RS_WARPS * 32 * RS_IPT;   // 4096 keys per tile
+constexpr int RS_WARPS = 8;                // radix sort: 8 warps x 32 lanes x ipt items per tile
+constexpr int RS_IPT_MAX = 16;
+constexpr int RS_TILE_MAX = RS_WARPS * 32 * RS_IPT_MAX;   // 4096 keys per tile at most
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_IPT = 8;
 constexpr int SCAN_SEG = SCAN_THREADS * SCAN_IPT; // 2048 elements per scan segment
@@ -51,7 +51,7 @@ struct Status {
     int64_t counters[4]; // [0] soft interactions, [1] hard interactions
 };
 
-// A tile of at most RS_TILE consecutive particles inside one system.
+// A tile of at most ctx->tile consecutive particles inside one system.
 struct Chunk {
     int64_t start;
     int32_t len;
@@ -100,6 +100,7 @@ struct hybrid_ctx {
     std::vector<hy::Chunk> h_chunks;
     std::vector<hy::SysIO> h_io;
     int nchunks = 0;
+    int ipt = 16, tile = 4096;   // radix tile: 8 warps x 32 lanes x ipt keys, sized to fill the GPU
     bool tree_valid = false, have_soft = false, have_hard = false;
 
     // capacities
@@ -122,7 +123,7 @@ struct hybrid_ctx {
     hy::Buf ndelta, nside, norg;               // geometry (inspection + finalize)
     hy::Buf gflag, gscan, gnode, gfirst, gcount, gsys, gF, glo, ghi, ngroups_dev;
     // lists
-    hy::Buf lcnt, loff, list, stack, counter, io_dev, energy_dev;
+    hy::Buf lcnt, loff, list, stack, counter, io_dev, energy_dev, wstart, wmap;
     int last_walk_mode = 0;
 
     // profiling
@@ -134,6 +135,21 @@ struct hybrid_ctx {
 
     // host pinned status
     hy::Status *h_status = nullptr;
+
+    // CUDA graphs of op sequences (one per sequence, buffer generation and
+    // parity of the state-buffer swaps done by the tree builds)
+    int swaps = 0;          // parity of x <-> xa swaps so far
+    int64_t gen = 0;        // bumped by every (re)allocation
+    bool use_graphs = true;
+    struct GraphEntry {
+        uint64_t sig;
+        int parity, net_swaps;
+        int64_t gen, nlaunch;
+        cudaGraphExec_t exec;
+        std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+    };
+    std::vector<GraphEntry> graphs;
+    bool capturing = false;
 };
 
 namespace hy {
@@ -148,8 +164,11 @@ void prof_end(hybrid_ctx *c, int kind, cudaEvent_t e0);
 // ---- scans (scan.cu) ----
 // Exclusive scan of n uint32 values (n from *d_n when d_n != null, else n_host),
 // in place; *d_total (optional) receives the sum. n_max bounds the grid.
-void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total);
-void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total);
+// always = true: runs even after a recorded failure (the sort's scans).
+void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
+              bool always = false);
+void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
+              bool always = false);
 
 // ---- tree (tree.cu) ----
 void launch_box(hybrid_ctx *c);
@@ -162,8 +181,11 @@ void launch_groups(hybrid_ctx *c);
 void launch_walk(hybrid_ctx *c, int mode);   // mode bit 0 soft, bit 1 hard
 
 // ---- pair kernels (pair.cu) ----
-void launch_pair_soft(hybrid_ctx *c);
-void launch_pair_hard(hybrid_ctx *c);
+// cells and far particles of the last walk -> soft accelerations (zeroed first)
+void launch_pair_far(hybrid_ctx *c);
+// near particles of the last walk: mode bit 0 adds F (1 - K) to the soft
+// accelerations (after launch_pair_far), bit 1 writes F K as the hard ones
+void launch_pair_near(hybrid_ctx *c, int mode);
 
 // ---- integrator and io (integrate.cu) ----
 void launch_copy_in(hybrid_ctx *c, const SysIO *d_io, bool with_acc);

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "hy_internal.cuh"
@@ -22,6 +23,11 @@ namespace hy {
 bool ensure(hybrid_ctx *c, Buf &b, size_t bytes)
 {
     if (b.p && b.bytes >= bytes) return true;
+    if (c->capturing) {   // no allocation inside a graph capture: every buffer is sized beforehand
+        set_err(c, "buffer growth requested during graph capture");
+        return false;
+    }
+    c->gen++;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -142,7 +148,7 @@ bool alloc_nodes(hybrid_ctx *c, int64_t cap)
                    &c->rd2b})
         ok = ok && ensure(c, *b, n * 4);
     ok = ok && ensure(c, c->rec, n * 8);
-    ok = ok && ensure(c, c->rhist, (size_t)(LEVELS + 1) * ((n + RS_TILE - 1) / RS_TILE) * 4);
+    ok = ok && ensure(c, c->rhist, (size_t)(LEVELS + 1) * ((n + 1023) / 1024) * 4);
     for (Buf *b : {&c->nM, &c->ncx, &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nrb, &c->nhr, &c->ndelta, &c->nside})
         ok = ok && ensure(c, *b, n * 8);
     ok = ok && ensure(c, c->norg, n * 24);
@@ -170,7 +176,7 @@ bool reserve(hybrid_ctx *c)
         ok = ok && ensure(c, c->keys[0], n * 8) && ensure(c, c->keys[1], n * 8);
         ok = ok && ensure(c, c->vals[0], n * 4) && ensure(c, c->vals[1], n * 4);
         ok = ok && ensure(c, c->gF, n * sizeof(GroupF)) && ensure(c, c->glo, n * 24) && ensure(c, c->ghi, n * 24);
-        ok = ok && ensure(c, c->lcnt, (3 * n + 2) * 8);
+        ok = ok && ensure(c, c->lcnt, (3 * n + 2) * 8) && ensure(c, c->wstart, (n + 2) * 4);
         if (ok) {
             c->capN = N;
             c->capGroups = N;
@@ -194,6 +200,8 @@ bool reserve(hybrid_ctx *c)
         ok = ok && ensure(c, c->list, (size_t)std::max<int64_t>(1 << 20, 128 * N) * 4);
         if (ok) c->capList = std::max<int64_t>(1 << 20, 128 * N);
     }
+    // pair work items: at most one per group plus one per 256 list entries
+    ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 4);
     if (c->capStack == 0) c->capStack = 4096;
     ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * c->capStack * 4);
     // scratch of the scans: the longest scan is over max(N, nodes, 3 groups + 1, tiles x 256)
@@ -252,15 +260,20 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
     }
     c->S = S;
     c->N = c->h_off[S];
+    // radix tiles: the largest of 512..4096 keys that still gives about 4 tiles per SM
+    c->ipt = 16;
+    while (c->ipt > 2 && c->N / (RS_WARPS * 32 * c->ipt) < 4 * c->nsm) c->ipt >>= 1;
+    c->tile = RS_WARPS * 32 * c->ipt;
+    const int tile = c->tile;
     c->h_chunks.clear();
     for (int s = 0; s < S; ++s) {
         const int first = (int)c->h_chunks.size();
         const int64_t n = c->h_off[s + 1] - c->h_off[s];
-        const int nch = (int)((n + RS_TILE - 1) / RS_TILE);
+        const int nch = (int)((n + tile - 1) / tile);
         for (int k = 0; k < nch; ++k) {
             Chunk ch;
-            ch.start = c->h_off[s] + (int64_t)k * RS_TILE;
-            ch.len = (int)std::min<int64_t>(RS_TILE, n - (int64_t)k * RS_TILE);
+            ch.start = c->h_off[s] + (int64_t)k * tile;
+            ch.len = (int)std::min<int64_t>(tile, n - (int64_t)k * tile);
             ch.sys = s;
             ch.first_chunk = first;
             ch.nchunk = nch;
@@ -302,7 +315,7 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
 }
 
 // ---- ops ----
-enum OpKind { OP_KICKS, OP_BUILD, OP_WALK, OP_PAIR_H, OP_PAIR_S };
+enum OpKind { OP_KICKS, OP_BUILD, OP_WALK, OP_PAIR_FAR, OP_PAIR_NEAR };
 struct Op {
     int kind = OP_BUILD;
     int mode = 0;
@@ -335,11 +348,11 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
     case OP_WALK:
         launch_walk(c, o.mode);
         break;
-    case OP_PAIR_H:
-        launch_pair_hard(c);
+    case OP_PAIR_FAR:
+        launch_pair_far(c);
         break;
-    case OP_PAIR_S:
-        launch_pair_soft(c);
+    case OP_PAIR_NEAR:
+        launch_pair_near(c, o.mode);
         break;
     }
 }
@@ -359,17 +372,158 @@ hybrid_status clear_status(hybrid_ctx *c)
     return e == cudaSuccess ? HYBRID_OK : cuda_fail(c, e, "status reset");
 }
 
+void swap_state(hybrid_ctx *c)
+{
+    for (int f = 0; f < 7; ++f) std::swap(c->x[f], c->xa[f]);
+    std::swap(c->id, c->ida);
+    std::swap(c->orig, c->origa);
+    c->swaps ^= 1;
+}
+
+// Adds the elapsed times of recorded (kind, start, end) event pairs; the
+// stream has been synchronised by the caller.
+void prof_collect(hybrid_ctx *c, const std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> &ev)
+{
+    for (auto &u : ev) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, u.second.first, u.second.second) == cudaSuccess) {
+            c->prof_ms[u.first] += t;
+            c->prof_n[u.first] += 1;
+        }
+    }
+    cudaGetLastError();
+}
+
+void drop_graphs(hybrid_ctx *c)
+{
+    for (auto &g : c->graphs) {
+        cudaGraphExecDestroy(g.exec);
+        for (auto &u : g.events) {
+            c->ev_pool.push_back(u.second.first);
+            c->ev_pool.push_back(u.second.second);
+        }
+    }
+    c->graphs.clear();
+}
+
+uint64_t ops_signature(const hybrid_ctx *c, const std::vector<Op> &ops)
+{
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)c->N);
+    mix((uint64_t)c->S);
+    mix((uint64_t)c->nchunks);
+    mix((uint64_t)c->ipt);
+    mix((uint64_t)c->prof);
+    for (const Op &o : ops) {
+        mix((uint64_t)o.kind);
+        mix((uint64_t)o.mode);
+        mix((uint64_t)o.nk);
+        mix((uint64_t)o.dmode);
+        for (int k = 0; k < o.nk; ++k) mix((uint64_t)(o.which[k] * 4 + o.kmode[k]));
+    }
+    return h;
+}
+
+// Captures ops as a CUDA graph (or finds the cached one) and launches it.
+// Returns false when graphs cannot be used; the ops are then not enqueued.
+bool launch_as_graph(hybrid_ctx *c, const std::vector<Op> &ops, std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> **events)
+{
+    if (!c->use_graphs || c->st == nullptr) return false;
+    const uint64_t sig = ops_signature(c, ops);
+    for (auto &g : c->graphs) {
+        if (g.sig == sig && g.parity == c->swaps && g.gen == c->gen) {
+            if (cudaGraphLaunch(g.exec, c->st) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (g.net_swaps) swap_state(c);
+            c->launches += g.nlaunch;
+            *events = &g.events;
+            return true;
+        }
+    }
+    // make sure the profiling events exist before capturing
+    if (c->prof)
+        while (c->ev_pool.size() < 4 * ops.size() + 64) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->ev_pool.push_back(e);
+        }
+    const int parity0 = c->swaps;
+    const int64_t gen0 = c->gen, l0 = c->launches;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> saved;
+    saved.swap(c->ev_used);
+    cudaGraph_t graph = nullptr;
+    c->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (size_t i = 0; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
+        e = cudaStreamEndCapture(c->st, &graph);
+    }
+    c->capturing = false;
+    cudaGraphExec_t exec = nullptr;
+    if (e == cudaSuccess && c->gen == gen0) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess || c->gen != gen0 || !exec) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        if (c->swaps != parity0) swap_state(c);   // undo the host side of the capture
+        for (auto &u : c->ev_used) {
+            c->ev_pool.push_back(u.second.first);
+            c->ev_pool.push_back(u.second.second);
+        }
+        c->ev_used.swap(saved);
+        c->launches = l0;
+        c->use_graphs = false;
+        return false;
+    }
+    hybrid_ctx::GraphEntry g;
+    g.sig = sig;
+    g.parity = parity0;
+    g.net_swaps = c->swaps != parity0;
+    g.gen = gen0;
+    g.nlaunch = c->launches - l0;
+    g.exec = exec;
+    g.events.swap(c->ev_used);
+    c->ev_used.swap(saved);
+    // the capture already moved the host-side pointers to their post-graph state
+    if (cudaGraphLaunch(exec, c->st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(exec);
+        if (g.net_swaps) swap_state(c);
+        c->launches = l0;
+        c->use_graphs = false;
+        return false;
+    }
+    c->graphs.push_back(std::move(g));
+    *events = &c->graphs.back().events;
+    return true;
+}
+
 hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
 {
     size_t start = 0;
     for (int attempt = 0; attempt < 12; ++attempt) {
-        for (size_t i = start; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
+        std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *gev = nullptr;
+        if (!(attempt == 0 && launch_as_graph(c, ops, &gev)))
+            for (size_t i = start; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(c, le, "kernel launch");
         Status s;
         hybrid_status r = read_status(c, &s);
         if (r != HYBRID_OK) return r;
+        if (c->prof) {
+            if (gev) prof_collect(c, *gev);
+            prof_collect(c, c->ev_used);
+            for (auto &u : c->ev_used) {
+                c->ev_pool.push_back(u.second.first);
+                c->ev_pool.push_back(u.second.second);
+            }
+            c->ev_used.clear();
+        }
         if (s.code == 0) return HYBRID_OK;
+        drop_graphs(c);
         if (s.code != HYBRID_ECAPACITY) {
             set_err(c, "device failure %d at op %d", s.code, s.where);
             clear_status(c);
@@ -382,6 +536,7 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
             const int64_t cap = s.need[1] + s.need[1] / 4 + 1024;
             ok = ok && ensure(c, c->list, (size_t)cap * 4);
             if (ok) c->capList = cap;
+            ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 4);
         }
         if (s.need[2] > c->capStack) {
             ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * s.need[2] * 4);
@@ -428,8 +583,8 @@ std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid)
     if (!valid) {
         ops.push_back(simple(OP_BUILD));
         ops.push_back(simple(OP_WALK, 3));
-        ops.push_back(simple(OP_PAIR_H));
-        ops.push_back(simple(OP_PAIR_S));
+        ops.push_back(simple(OP_PAIR_FAR));
+        ops.push_back(simple(OP_PAIR_NEAR, 3));
     }
     int pw[8], pm[8], np = 0;
     auto add = [&](int which, int mode) {
@@ -446,8 +601,8 @@ std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid)
             np = 0;
             ops.push_back(simple(OP_BUILD));
             ops.push_back(simple(OP_WALK, k == nh ? 3 : 2));
-            ops.push_back(simple(OP_PAIR_H));
-            if (k == nh) ops.push_back(simple(OP_PAIR_S));
+            if (k == nh) ops.push_back(simple(OP_PAIR_FAR));
+            ops.push_back(simple(OP_PAIR_NEAR, k == nh ? 3 : 2));
             add(1, 2);
         }
         add(0, 1);
@@ -495,6 +650,10 @@ hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stre
         return HYBRID_ECUDA;
     }
     c->walk_warps = c->nsm * 16;
+    {   // HYBRID_GRAPHS=0 enqueues every op directly instead of replaying captured CUDA graphs
+        const char *g = getenv("HYBRID_GRAPHS");
+        if (g && g[0] == '0') c->use_graphs = false;
+    }
     bool ok = ensure(c, c->status, sizeof(Status)) && ensure(c, c->counter, 16 * 8) && ensure(c, c->lvl, 1024) &&
               ensure(c, c->ngroups_dev, 64);
     if (!ok) {
@@ -529,7 +688,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
                   &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
                   &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
                   &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,
-                  &c->io_dev, &c->energy_dev};
+                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (int f = 0; f < 7; ++f) {
@@ -540,6 +699,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
         if (c->acc_s[d].p) cudaFree(c->acc_s[d].p);
         if (c->acc_h[d].p) cudaFree(c->acc_h[d].p);
     }
+    drop_graphs(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (auto &u : c->ev_used) {
         cudaEventDestroy(u.second.first);
@@ -582,7 +742,10 @@ hybrid_status force_call(hybrid_ctx *c, hybrid_system *sys, bool soft)
     for (int d = 0; d < 3; ++d) (soft ? o.as : o.ah)[d] = a[d];
     cudaError_t e = cudaMemcpyAsync(c->io_dev.p, &o, sizeof(SysIO), cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload");
-    hybrid_status r = run_ops(c, {simple(OP_WALK, soft ? 1 : 2), simple(soft ? OP_PAIR_S : OP_PAIR_H)});
+    std::vector<Op> ops = {simple(OP_WALK, soft ? 1 : 2)};
+    if (soft) ops.push_back(simple(OP_PAIR_FAR));
+    ops.push_back(simple(OP_PAIR_NEAR, soft ? 1 : 2));
+    hybrid_status r = run_ops(c, ops);
     if (r != HYBRID_OK) return r;
     launch_copy_out(c, (const SysIO *)c->io_dev.p, false, soft, !soft);
     (soft ? c->have_soft : c->have_hard) = true;
@@ -734,18 +897,34 @@ hybrid_status hybrid_lists_copy(hybrid_ctx *c, int64_t *counts, int64_t *entries
     std::vector<uint64_t> off;
     if (!d2h(c, off, c->lcnt, 3 * ng + 1) || cudaStreamSynchronize(c->st) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "list copy");
+    // stored as cells, far particles, near particles; reported as cells, soft
+    // particles (far then near) and hard particles (near, when the walk asked for them)
     const uint64_t total = off[3 * ng];
-    for (int64_t g = 0; g < ng; ++g)
-        for (int k = 0; k < 3; ++k) counts[3 * g + k] = (int64_t)(off[k * ng + g + 1] - off[k * ng + g]);
+    const bool soft = c->last_walk_mode & 1, hard = (c->last_walk_mode >> 1) & 1;
+    int64_t need = 0;
+    for (int64_t g = 0; g < ng; ++g) {
+        const int64_t nc = (int64_t)(off[g + 1] - off[g]), nf = (int64_t)(off[ng + g + 1] - off[ng + g]),
+                      nn = (int64_t)(off[2 * ng + g + 1] - off[2 * ng + g]);
+        counts[3 * g + 0] = soft ? nc : 0;
+        counts[3 * g + 1] = soft ? nf + nn : 0;
+        counts[3 * g + 2] = hard ? nn : 0;
+        need += counts[3 * g] + counts[3 * g + 1] + counts[3 * g + 2];
+    }
     if (!entries) return HYBRID_OK;
-    if ((int64_t)total > cap_entries) return HYBRID_EINVAL;
+    if (need > cap_entries) return HYBRID_EINVAL;
     std::vector<uint32_t> L;
     if (!d2h(c, L, c->list, total) || cudaStreamSynchronize(c->st) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "list copy");
     int64_t o = 0;
-    for (int64_t g = 0; g < ng; ++g)
-        for (int k = 0; k < 3; ++k)
-            for (uint64_t j = off[k * ng + g]; j < off[k * ng + g + 1]; ++j) entries[o++] = L[j];
+    for (int64_t g = 0; g < ng; ++g) {
+        if (soft) {
+            for (uint64_t j = off[g]; j < off[g + 1]; ++j) entries[o++] = L[j];
+            for (uint64_t j = off[ng + g]; j < off[ng + g + 1]; ++j) entries[o++] = L[j];
+            for (uint64_t j = off[2 * ng + g]; j < off[2 * ng + g + 1]; ++j) entries[o++] = L[j];
+        }
+        if (hard)
+            for (uint64_t j = off[2 * ng + g]; j < off[2 * ng + g + 1]; ++j) entries[o++] = L[j];
+    }
     return HYBRID_OK;
 }
 
@@ -764,6 +943,7 @@ hybrid_status hybrid_interactions(hybrid_ctx *c, int64_t *soft, int64_t *hard)
 hybrid_status hybrid_profile(hybrid_ctx *c, int enable)
 {
     if (!c) return HYBRID_EINVAL;
+    if (c->prof != (enable != 0)) drop_graphs(c);
     c->prof = enable != 0;
     return HYBRID_OK;
 }
@@ -772,11 +952,8 @@ hybrid_status hybrid_profile_read(hybrid_ctx *c, int kind, double *ms, int64_t *
 {
     if (!c || kind < 0 || kind >= PROF_KINDS) return HYBRID_EINVAL;
     if (cudaStreamSynchronize(c->st) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "profile sync");
+    prof_collect(c, c->ev_used);
     for (auto &u : c->ev_used) {
-        float t = 0.0f;
-        cudaEventElapsedTime(&t, u.second.first, u.second.second);
-        c->prof_ms[u.first] += t;
-        c->prof_n[u.first] += 1;
         c->ev_pool.push_back(u.second.first);
         c->ev_pool.push_back(u.second.second);
     }

@@ -16,60 +16,64 @@ struct StatePtrs {
     void *as[3], *ah[3];
 };
 
-// chunk c covers particles [start, start + len) of system sys
-__global__ void __launch_bounds__(256) k_copy_in(const Chunk *__restrict__ chunks, int nchunks,
+// system of batch position i: binary search over the offsets (S + 1 entries)
+__device__ __forceinline__ int sys_of(const int64_t *__restrict__ off, int S, int64_t i)
+{
+    int lo = 0, hi = S;   // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_copy_in(int64_t N, int S, const int64_t *__restrict__ off,
                                                  const SysIO *__restrict__ io, StatePtrs w, int prec, int with_acc)
 {
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const Chunk ch = chunks[c];
-        const SysIO s = io[ch.sys];
-        const int64_t loc0 = ch.start - s.off;
-        for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
-            const int64_t li = loc0 + t, gi = ch.start + t;
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < N; gi += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sys_of(off, S, gi);
+        const SysIO &y = io[s];
+        const int64_t li = gi - y.off;
 #pragma unroll
-            for (int f = 0; f < 7; ++f) w.x[f][gi] = s.x[f][li];
-            w.id[gi] = s.id ? s.id[li] : (int32_t)li;
-            w.orig[gi] = (int32_t)li;
-            w.psys[gi] = ch.sys;
-            if (with_acc) {
-                for (int d = 0; d < 3; ++d) {
-                    if (prec == 1) {
-                        ((float *)w.as[d])[gi] = ((const float *)s.as[d])[li];
-                        ((float *)w.ah[d])[gi] = ((const float *)s.ah[d])[li];
-                    } else {
-                        ((double *)w.as[d])[gi] = ((const double *)s.as[d])[li];
-                        ((double *)w.ah[d])[gi] = ((const double *)s.ah[d])[li];
-                    }
+        for (int f = 0; f < 7; ++f) w.x[f][gi] = y.x[f][li];
+        w.id[gi] = y.id ? y.id[li] : (int32_t)li;
+        w.orig[gi] = (int32_t)li;
+        w.psys[gi] = s;
+        if (with_acc) {
+            for (int d = 0; d < 3; ++d) {
+                if (prec == 1) {
+                    ((float *)w.as[d])[gi] = ((const float *)y.as[d])[li];
+                    ((float *)w.ah[d])[gi] = ((const float *)y.ah[d])[li];
+                } else {
+                    ((double *)w.as[d])[gi] = ((const double *)y.as[d])[li];
+                    ((double *)w.ah[d])[gi] = ((const double *)y.ah[d])[li];
                 }
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_copy_out(const Chunk *__restrict__ chunks, int nchunks,
+__global__ void __launch_bounds__(256) k_copy_out(int64_t N, const int32_t *__restrict__ psys,
                                                   const SysIO *__restrict__ io, StatePtrs w, int prec, int state,
                                                   int acc_s, int acc_h, const Status *st)
 {
     if (st->code) return;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const Chunk ch = chunks[c];
-        const SysIO s = io[ch.sys];
-        const int64_t loc0 = ch.start - s.off;
-        for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
-            const int64_t li = loc0 + t, gi = ch.start + t;
-            if (state) {
+    for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < N; gi += (int64_t)gridDim.x * blockDim.x) {
+        const SysIO &y = io[psys[gi]];
+        const int64_t li = gi - y.off;
+        if (state) {
 #pragma unroll
-                for (int f = 0; f < 7; ++f) s.x[f][li] = w.x[f][gi];
-                if (s.id) s.id[li] = w.id[gi];
-            }
-            for (int d = 0; d < 3; ++d) {
-                if (prec == 1) {
-                    if (acc_s) ((float *)s.as[d])[li] = ((const float *)w.as[d])[gi];
-                    if (acc_h) ((float *)s.ah[d])[li] = ((const float *)w.ah[d])[gi];
-                } else {
-                    if (acc_s) ((double *)s.as[d])[li] = ((const double *)w.as[d])[gi];
-                    if (acc_h) ((double *)s.ah[d])[li] = ((const double *)w.ah[d])[gi];
-                }
+            for (int f = 0; f < 7; ++f) y.x[f][li] = w.x[f][gi];
+            if (y.id) y.id[li] = w.id[gi];
+        }
+        for (int d = 0; d < 3; ++d) {
+            if (prec == 1) {
+                if (acc_s) ((float *)y.as[d])[li] = ((const float *)w.as[d])[gi];
+                if (acc_h) ((float *)y.ah[d])[li] = ((const float *)w.ah[d])[gi];
+            } else {
+                if (acc_s) ((double *)y.as[d])[li] = ((const double *)w.as[d])[gi];
+                if (acc_h) ((double *)y.ah[d])[li] = ((const double *)w.ah[d])[gi];
             }
         }
     }
@@ -141,13 +145,13 @@ __global__ void __launch_bounds__(256) k_drift_ext(int64_t n, double *x, double 
 // Softened energies by direct FP64 summation: one thread per sink, sources of
 // the same system staged through shared memory; per-system sums by atomics.
 constexpr int EN_THREADS = 256;
-__global__ void __launch_bounds__(EN_THREADS) k_energy(const Chunk *__restrict__ chunks, int nchunks,
+__global__ void __launch_bounds__(EN_THREADS) k_energy(const Chunk *__restrict__ chunks, int nchunks, int SUB,
                                                        const int64_t *__restrict__ off, StatePtrs w,
                                                        const SysParams *__restrict__ sp, double *out)
 {
     __shared__ double4_32a tile[EN_THREADS];
     __shared__ double red[2][EN_THREADS / 32];
-    constexpr int SUB = RS_TILE / EN_THREADS;   // sink tiles per chunk
+    // SUB = sink tiles of EN_THREADS per radix chunk
     for (int b = blockIdx.x; b < nchunks * SUB; b += gridDim.x) {
         const Chunk ch = chunks[b / SUB];
         const int t0 = (b % SUB) * EN_THREADS;
@@ -218,18 +222,22 @@ StatePtrs state_ptrs(hybrid_ctx *c)
 
 }  // namespace
 
+static int grid_n(hybrid_ctx *c, int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)c->nsm * 8));
+}
+
 void launch_copy_in(hybrid_ctx *c, const SysIO *d_io, bool with_acc)
 {
-    k_copy_in<<<std::min(c->nchunks, c->nsm * 8), 256, 0, c->st>>>((const Chunk *)c->chunks_dev.p, c->nchunks, d_io,
-                                                                    state_ptrs(c), c->p.precision, with_acc ? 1 : 0);
+    k_copy_in<<<grid_n(c, c->N), 256, 0, c->st>>>(c->N, c->S, (const int64_t *)c->off_dev.p, d_io, state_ptrs(c),
+                                                   c->p.precision, with_acc ? 1 : 0);
     c->launches++;
 }
 
 void launch_copy_out(hybrid_ctx *c, const SysIO *d_io, bool state, bool acc_s, bool acc_h)
 {
-    k_copy_out<<<std::min(c->nchunks, c->nsm * 8), 256, 0, c->st>>>((const Chunk *)c->chunks_dev.p, c->nchunks, d_io,
-                                                                     state_ptrs(c), c->p.precision, state, acc_s, acc_h,
-                                                                     status_dev(c));
+    k_copy_out<<<grid_n(c, c->N), 256, 0, c->st>>>(c->N, (const int32_t *)c->psys.p, d_io, state_ptrs(c),
+                                                    c->p.precision, state, acc_s, acc_h, status_dev(c));
     c->launches++;
 }
 
@@ -282,8 +290,9 @@ void launch_drift_ext(hybrid_ctx *c, const hybrid_system *s, double dt)
 void launch_energy(hybrid_ctx *c, double *d_out)
 {
     cudaMemsetAsync(d_out, 0, (size_t)2 * c->S * sizeof(double), c->st);
-    k_energy<<<std::min(c->nchunks * (RS_TILE / EN_THREADS), c->nsm * 8), EN_THREADS, 0, c->st>>>(
-        (const Chunk *)c->chunks_dev.p, c->nchunks, (const int64_t *)c->off_dev.p, state_ptrs(c),
+    const int sub = c->tile / EN_THREADS;
+    k_energy<<<std::min(c->nchunks * sub, c->nsm * 8), EN_THREADS, 0, c->st>>>(
+        (const Chunk *)c->chunks_dev.p, c->nchunks, sub, (const int64_t *)c->off_dev.p, state_ptrs(c),
         (const SysParams *)c->sp_dev.p, d_out);
     c->launches++;
 }

@@ -52,7 +52,7 @@ template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T *data, int64_t n_host, const int64_t *d_n,
                                                                uint64_t *bsum, const Status *st)
 {
-    if (st->code) return;
+    if (st && st->code) return;
     const int64_t n = d_n ? *d_n : n_host;
     const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
     for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T *data, int
 __global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *bsum, int64_t n_host, const int64_t *d_n,
                                                      uint64_t *d_total, const Status *st)
 {
-    if (st->code) return;
+    if (st && st->code) return;
     const int64_t n = d_n ? *d_n : n_host;
     const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
     __shared__ uint64_t wsum[32];
@@ -104,7 +104,7 @@ template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(T *data, int64_t n_host, const int64_t *d_n,
                                                              const uint64_t *bsum, const Status *st)
 {
-    if (st->code) return;
+    if (st && st->code) return;
     const int64_t n = d_n ? *d_n : n_host;
     const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
     for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(T *data, int64_t n_h
 }
 
 template <typename T>
-static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
+                      bool always)
 {
     const int64_t nseg_max = (n_max + SCAN_SEG - 1) / SCAN_SEG;
     if (nseg_max <= 0) {
@@ -137,21 +138,23 @@ static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n
     ensure(c, c->blocksum, (size_t)nseg_max * sizeof(uint64_t));
     uint64_t *bs = (uint64_t *)c->blocksum.p;
     const int grid = (int)std::min<int64_t>(nseg_max, (int64_t)c->nsm * 8);
-    Status *st = status_dev(c);
+    Status *st = always ? nullptr : status_dev(c);
     k_scan_reduce<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
     k_scan_spine<<<1, 1024, 0, c->st>>>(bs, n_host, d_n, d_total, st);
     k_scan_down<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
     c->launches += 3;
 }
 
-void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
+              bool always)
 {
-    scan_impl<uint32_t>(c, data, n_host, d_n, n_max, d_total);
+    scan_impl<uint32_t>(c, data, n_host, d_n, n_max, d_total, always);
 }
 
-void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total)
+void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
+              bool always)
 {
-    scan_impl<uint64_t>(c, data, n_host, d_n, n_max, d_total);
+    scan_impl<uint64_t>(c, data, n_host, d_n, n_max, d_total, always);
 }
 
 }  // namespace hy

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(256) k_box(const double *__restrict__ x, const
                                              int nchunks, unsigned long long *bmin, unsigned long long *bmax,
                                              const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     __shared__ double sh[6][8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) k_box(const double *__restrict__ x, const
 __global__ void k_box_final(int S, const unsigned long long *bmin, const unsigned long long *bmax, SysBox *box,
                             const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     double lo[3], ext = 0.0;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restric
                                               const SysBox *__restrict__ box, uint64_t *__restrict__ key,
                                               uint32_t *__restrict__ val, const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const SysBox b = box[psys[i]];
         const uint32_t qx = cell_coord(x[i], b.lo[0], b.scale);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t *__restrict__
                                                     int nchunks, int shift, uint32_t *__restrict__ hist,
                                                     const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     __shared__ uint32_t h[256];
     const int lane = threadIdx.x & 31;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
@@ -194,13 +194,14 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t *__restrict__
     }
 }
 
+template <int IPT>
 __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restrict__ kin,
                                                        const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
                                                        uint32_t *__restrict__ vout,
                                                        const Chunk *__restrict__ chunks, int nchunks, int shift,
                                                        const uint32_t *__restrict__ offs, const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t base[256];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -210,11 +211,11 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restric
         for (int t = threadIdx.x; t < RS_WARPS * 256; t += blockDim.x) (&whist[0][0])[t] = 0;
         base[threadIdx.x] = offs[hist_slot(ch, c, threadIdx.x)];
         __syncthreads();
-        uint64_t k[RS_IPT];
-        uint32_t v[RS_IPT], r[RS_IPT];
-        const int wbase = w * 32 * RS_IPT;
+        uint64_t k[IPT];
+        uint32_t v[IPT], r[IPT];
+        const int wbase = w * 32 * IPT;
 #pragma unroll
-        for (int it = 0; it < RS_IPT; ++it) {
+        for (int it = 0; it < IPT; ++it) {
             const int li = wbase + it * 32 + lane;     // warp-striped: (it, lane) is input order
             const bool ok = li < ch.len;
             k[it] = ok ? kin[ch.start + li] : 0ull;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restric
         }
         __syncthreads();
 #pragma unroll
-        for (int it = 0; it < RS_IPT; ++it) {
+        for (int it = 0; it < IPT; ++it) {
             const int li = wbase + it * 32 + lane;
             if (li < ch.len) {
                 const uint32_t d = (uint32_t)(k[it] >> shift) & 0xffu;
@@ -271,7 +272,7 @@ struct PermArgs {
 
 __global__ void __launch_bounds__(256) k_permute(PermArgs a, const Status *st)
 {
-    if (st->code) return;
+    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.N; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = a.src[i];
         double v[7];
@@ -393,7 +394,8 @@ __global__ void __launch_bounds__(256) k_records(int64_t N, const int8_t *__rest
     }
 }
 
-constexpr int REC_TILE = RS_TILE;   // 4096 records per tile, 8 warps x 32 lanes x 16
+constexpr int REC_IPT = 4;
+constexpr int REC_TILE = RS_WARPS * 32 * REC_IPT;   // 1024 records per tile
 constexpr int NLEV = LEVELS + 1;    // levels 0..21
 
 __global__ void __launch_bounds__(256) k_rec_hist(const unsigned long long *__restrict__ rec,
@@ -436,10 +438,10 @@ __global__ void __launch_bounds__(256) k_rec_scatter(const unsigned long long *_
         for (int k = threadIdx.x; k < RS_WARPS * NLEV; k += blockDim.x) (&whist[0][0])[k] = 0;
         if (threadIdx.x < NLEV) base[threadIdx.x] = hoff[(size_t)threadIdx.x * ntiles + t];
         __syncthreads();
-        uint32_t lv[RS_IPT], r[RS_IPT];
-        const int wbase = w * 32 * RS_IPT;
+        uint32_t lv[REC_IPT], r[REC_IPT];
+        const int wbase = w * 32 * REC_IPT;
 #pragma unroll
-        for (int it = 0; it < RS_IPT; ++it) {
+        for (int it = 0; it < REC_IPT; ++it) {
             const uint64_t li = b0 + wbase + it * 32 + lane;
             const bool ok = li < T;
             const uint32_t d = ok ? (uint32_t)(rec[li] >> 32) : 32u;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(256) k_rec_scatter(const unsigned long long *_
         }
         __syncthreads();
 #pragma unroll
-        for (int it = 0; it < RS_IPT; ++it) {
+        for (int it = 0; it < REC_IPT; ++it) {
             const uint64_t li = b0 + wbase + it * 32 + lane;
             if (li < T) {
                 const uint32_t dst = base[lv[it]] + whist[w][lv[it]] + r[it];
@@ -601,7 +603,25 @@ __device__ __forceinline__ void store_com(const MomArgs &a, uint32_t c, double M
     a.nB[c] = make_float4(l[0], l[1], l[2], 0.0f);
 }
 
-__global__ void __launch_bounds__(256) k_moments(MomArgs a, const Status *st)
+__device__ __forceinline__ void com_or_centre(const MomArgs &a, uint32_t c, double M, double t0, double t1,
+                                              double t2, double &p0, double &p1, double &p2)
+{
+    if (M > 0.0) {
+        p0 = t0 / M;
+        p1 = t1 / M;
+        p2 = t2 / M;
+    } else {   // massless cell: its geometric centre
+        double o[3], sd;
+        const uint32_t f = a.nfirst[c];
+        cell_geom(a.box[a.psys[f]], a.key[f], a.nlevel[c], o, &sd);
+        p0 = o[0] + 0.5 * sd;
+        p1 = o[1] + 0.5 * sd;
+        p2 = o[2] + 0.5 * sd;
+    }
+}
+
+// leaves: sums over their particles
+__global__ void __launch_bounds__(256) k_mom_leaves(MomArgs a, const Status *st)
 {
     if (st->code) return;
     const uint32_t total = a.lvl[LEVELS + 1];
@@ -618,62 +638,43 @@ __global__ void __launch_bounds__(256) k_moments(MomArgs a, const Status *st)
             a.leafof[i] = c;
         }
         double c0, c1, c2;
-        if (M > 0.0) {
-            c0 = s0 / M;
-            c1 = s1 / M;
-            c2 = s2 / M;
-        } else {   // massless cell: its geometric centre
-            double o[3], sd;
-            cell_geom(a.box[a.psys[f]], a.key[f], a.nlevel[c], o, &sd);
-            c0 = o[0] + 0.5 * sd;
-            c1 = o[1] + 0.5 * sd;
-            c2 = o[2] + 0.5 * sd;
-        }
+        com_or_centre(a, c, M, s0, s1, s2, c0, c1, c2);
         double B2 = 0.0;
         for (uint32_t i = f; i < f + n; ++i) {
             const double d0 = a.x[i] - c0, d1 = a.y[i] - c1, d2 = a.z[i] - c2;
             B2 += a.m[i] * (d0 * d0 + d1 * d1 + d2 * d2);
         }
         store_com(a, c, M, c0, c1, c2, B2);
-        // climb while this thread completes the last child of the parent
-        uint32_t p = a.nparent[c];
-        while (p != NONE) {
-            __threadfence();
-            const uint32_t k = a.nnch[p];
-            if (atomicAdd(&a.done[p], 1u) != k - 1u) break;
-            __threadfence();
-            const uint32_t ch = a.nchild[p];
-            double Mp = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
-            for (uint32_t j = 0; j < k; ++j) {
-                const double Mj = __ldcg(&a.M[ch + j]);
-                Mp += Mj;
-                t0 += Mj * __ldcg(&a.cx[ch + j]);
-                t1 += Mj * __ldcg(&a.cy[ch + j]);
-                t2 += Mj * __ldcg(&a.cz[ch + j]);
-            }
-            double p0, p1, p2;
-            if (Mp > 0.0) {
-                p0 = t0 / Mp;
-                p1 = t1 / Mp;
-                p2 = t2 / Mp;
-            } else {
-                double o[3], sd;
-                const uint32_t fp = a.nfirst[p];
-                cell_geom(a.box[a.psys[fp]], a.key[fp], a.nlevel[p], o, &sd);
-                p0 = o[0] + 0.5 * sd;
-                p1 = o[1] + 0.5 * sd;
-                p2 = o[2] + 0.5 * sd;
-            }
-            double Bp = 0.0;
-            for (uint32_t j = 0; j < k; ++j) {
-                const double Mj = __ldcg(&a.M[ch + j]);
-                const double d0 = __ldcg(&a.cx[ch + j]) - p0, d1 = __ldcg(&a.cy[ch + j]) - p1,
-                             d2 = __ldcg(&a.cz[ch + j]) - p2;
-                Bp += __ldcg(&a.B2[ch + j]) + Mj * (d0 * d0 + d1 * d1 + d2 * d2);
-            }
-            store_com(a, p, Mp, p0, p1, p2, Bp);
-            p = a.nparent[p];
+    }
+}
+
+// internal nodes of one level: sums over their children (done by the
+// previous launch); B2 by the parallel-axis rule
+__global__ void __launch_bounds__(256) k_mom_level(int lev, MomArgs a, const Status *st)
+{
+    if (st->code) return;
+    const uint32_t l0 = a.lvl[lev], l1 = a.lvl[lev + 1];
+    for (uint32_t p = l0 + blockIdx.x * blockDim.x + threadIdx.x; p < l1; p += gridDim.x * blockDim.x) {
+        const uint32_t k = a.nnch[p];
+        if (k == 0) continue;
+        const uint32_t ch = a.nchild[p];
+        double Mp = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
+        for (uint32_t j = 0; j < k; ++j) {
+            const double Mj = a.M[ch + j];
+            Mp += Mj;
+            t0 += Mj * a.cx[ch + j];
+            t1 += Mj * a.cy[ch + j];
+            t2 += Mj * a.cz[ch + j];
         }
+        double p0, p1, p2;
+        com_or_centre(a, p, Mp, t0, t1, t2, p0, p1, p2);
+        double Bp = 0.0;
+        for (uint32_t j = 0; j < k; ++j) {
+            const double Mj = a.M[ch + j];
+            const double d0 = a.cx[ch + j] - p0, d1 = a.cy[ch + j] - p1, d2 = a.cz[ch + j] - p2;
+            Bp += a.B2[ch + j] + Mj * (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+        store_com(a, p, Mp, p0, p1, p2, Bp);
     }
 }
 
@@ -915,7 +916,7 @@ void launch_box(hybrid_ctx *c)
     Status *st = status_dev(c);
     cudaMemsetAsync(c->boxmin.p, 0xff, (size_t)3 * c->S * sizeof(unsigned long long), c->st);
     cudaMemsetAsync(c->boxmax.p, 0x00, (size_t)3 * c->S * sizeof(unsigned long long), c->st);
-    k_box<<<std::min(c->nchunks, c->nsm * 8), 256, 0, c->st>>>(
+    k_box<<<std::min(c->nchunks, c->nsm * 16), 256, 0, c->st>>>(
         (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const Chunk *)c->chunks_dev.p,
         c->nchunks, (unsigned long long *)c->boxmin.p, (unsigned long long *)c->boxmax.p, st);
     k_box_final<<<(c->S + 127) / 128, 128, 0, c->st>>>(c->S, (const unsigned long long *)c->boxmin.p,
@@ -933,15 +934,20 @@ void launch_keys_sort_permute(hybrid_ctx *c)
                                                     (const double *)c->x[2].p, (const int32_t *)c->psys.p,
                                                     (const SysBox *)c->box.p, k0, v0, st);
     c->launches++;
-    const int grid = std::min(c->nchunks, c->nsm * 4);
+    const int grid = std::min(c->nchunks, c->nsm * 8);
     uint32_t *hist = (uint32_t *)c->hist.p;
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 8 * pass;
         k_radix_hist<<<grid, 256, 0, c->st>>>(k0, (const Chunk *)c->chunks_dev.p, c->nchunks, shift, hist, st);
         c->launches++;
-        scan_u32(c, hist, (int64_t)c->nchunks * 256, nullptr, (int64_t)c->nchunks * 256, nullptr);
-        k_radix_scatter<<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, (const Chunk *)c->chunks_dev.p, c->nchunks, shift,
-                                                  hist, st);
+        scan_u32(c, hist, (int64_t)c->nchunks * 256, nullptr, (int64_t)c->nchunks * 256, nullptr, true);
+        const Chunk *chk = (const Chunk *)c->chunks_dev.p;
+        switch (c->ipt) {
+        case 2: k_radix_scatter<2><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
+        case 4: k_radix_scatter<4><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
+        case 8: k_radix_scatter<8><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
+        default: k_radix_scatter<16><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st);
+        }
         c->launches++;
         std::swap(k0, k1);
         std::swap(v0, v1);
@@ -968,6 +974,7 @@ void launch_keys_sort_permute(hybrid_ctx *c)
     for (int f = 0; f < 7; ++f) std::swap(c->x[f], c->xa[f]);
     std::swap(c->id, c->ida);
     std::swap(c->orig, c->origa);
+    c->swaps ^= 1;
 }
 
 bool launch_build_levels(hybrid_ctx *c)
@@ -1009,7 +1016,6 @@ void launch_moments(hybrid_ctx *c)
 {
     Status *st = status_dev(c);
     const int grid = grid_for(c, c->capNodes, 256, 8);
-    cudaMemsetAsync(c->ndone.p, 0, (size_t)c->capNodes * sizeof(uint32_t), c->st);
     cudaMemsetAsync(c->nbmax.p, 0, (size_t)c->capNodes * sizeof(unsigned long long), c->st);
     MomArgs a;
     a.lvl = (const uint32_t *)c->lvl.p;
@@ -1035,7 +1041,10 @@ void launch_moments(hybrid_ctx *c)
     a.nB = (float4 *)c->nB.p;
     a.done = (uint32_t *)c->ndone.p;
     a.leafof = (uint32_t *)c->leafof.p;
-    k_moments<<<grid, 256, 0, c->st>>>(a, st);
+    k_mom_leaves<<<grid, 256, 0, c->st>>>(a, st);
+    const int gridl = grid_for(c, c->N / 4 + 1024, 256, 4);
+    for (int lev = LEVELS - 1; lev >= 0; --lev) k_mom_level<<<gridl, 256, 0, c->st>>>(lev, a, st);
+    c->launches += LEVELS;
     const int gridp = grid_for(c, c->N, 256, 8);
     if (c->p.precision == 0)
         k_bmax<true><<<gridp, 256, 0, c->st>>>(

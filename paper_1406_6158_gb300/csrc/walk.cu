@@ -5,9 +5,13 @@
 // One warp walks one group at a time, starting at its system's root. Each
 // iteration pops up to 32 pending cells (one per lane) from a per-warp stack,
 // tests them, and with warp ballots/scans appends:
-//   soft cells      taken whole: r >= r_b and r >= R2 + b_max,
-//   soft particles  members of leaves that the soft walk opens,
-//   hard particles  members of leaves with r < R2 + b_max,
+//   cells           taken whole: r >= r_b and r >= R2 + b_max (K = 0 for
+//                   every pair, weight 1),
+//   far particles   members of leaves the soft walk opens with
+//                   r >= R2 + b_max (K = 0 for every pair, weight 1),
+//   near particles  members of leaves with r < R2 + b_max, reached by the
+//                   soft or the hard walk: the only pairs where K can be
+//                   non-zero (soft weight 1 - K, hard weight K),
 // and pushes the children of opened cells. r is the distance from the cell's
 // centre of mass to the group box. The count pass sizes every list, a scan
 // turns counts into offsets, and the fill pass writes the lists.
@@ -110,7 +114,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
         const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gg, 0);
         if (g >= ng) break;
         const uint32_t s = a.gsys[g];
-        const bool wh0 = want_hard && a.sp[s].has_hard;
+        const bool has_hard = a.sp[s].has_hard != 0;
+        const bool wh0 = want_hard && has_hard;
         float cx = 0, cy = 0, cz = 0, lx = 0, ly = 0, lz = 0, hx = 0, hy = 0, hz = 0;
         double blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
         if (F64) {
@@ -162,7 +167,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
                     const double d = dist_box_f64(D.x, D.y, D.z, blo, bhi);
                     const double hr = a.hr[c];
                     accept = (d >= a.rb[c]) && (d >= hr);
-                    near = wh && (d < hr);
+                    near = has_hard && (d < hr);
                 } else {
                     const float4 A = a.nA[c], B = a.nB[c];
                     const float2 cr = a.crit[c];
@@ -171,15 +176,16 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
                     const float rz = fmaxf(fabsf((A.z - cz) + (B.z - lz)) - hz, 0.0f);
                     const float d2 = rx * rx + ry * ry + rz * rz;
                     accept = d2 >= cr.x;
-                    near = wh && (d2 < cr.y);
+                    near = has_hard && (d2 < cr.y);
                 }
             }
             const bool leaf = (T.y == 0);
+            const bool open_s = ws && !accept;             // the soft walk goes on below c
+            const bool open_h = wh && near;                // the hard walk goes on below c
             const bool take_cell = valid && ws && accept;
-            const bool soft_leaf = valid && ws && !accept && leaf;
-            const bool hard_leaf = valid && near && leaf;
-            const bool open_s = ws && !accept;
-            const bool open = valid && !leaf && (open_s || near);
+            const bool soft_leaf = valid && leaf && open_s && !near;        // far particles
+            const bool hard_leaf = valid && leaf && (open_s || open_h) && near;   // near particles
+            const bool open = valid && !leaf && (open_s || open_h);
             // taken cells
             const unsigned bm = __ballot_sync(0xffffffffu, take_cell);
             if (FILL && take_cell) a.list[oc + nc + __popc(bm & ltmask)] = c;
@@ -216,7 +222,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
                     break;
                 }
                 if (open) {
-                    const uint32_t fl = ((uint32_t)open_s << 30) | ((uint32_t)near << 31);
+                    const uint32_t fl = ((uint32_t)open_s << 30) | ((uint32_t)open_h << 31);
                     for (uint32_t j = 0; j < k; ++j) stk[sp + ex + j] = (T.x + j) | fl;
                 }
                 sp += tot;

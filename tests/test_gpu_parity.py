@@ -199,10 +199,10 @@ def test_lists_and_forces(H, name, mk, kw, prec):
         eh = np.linalg.norm(g_h - a_h, axis=1)[nz] / np.linalg.norm(a_h, axis=1)[nz]
         assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
         assert np.all(np.linalg.norm(g_h, axis=1)[~nz] == 0.0)
-    si, hi = ctx.hybrid_interactions()
+    far, near = ctx.hybrid_interactions()   # the last evaluation was the soft force
     os_, oh = T.interactions(mode=3)
-    assert si == os_ or prec == 1
-    assert abs(si - os_) <= 1e-3 * os_
+    assert far + near == os_ or prec == 1
+    assert abs(far + near - os_) <= 1e-3 * os_
 
 
 def test_hard_lists_and_theta_zero(H):
@@ -280,8 +280,19 @@ def test_batched_equals_alone(H, prec):
     ctx.hybrid_step_batched(sysb, 2)
     for a, s in zip(alone, sysb):
         b = s.numpy()
-        for k in ("x", "y", "z", "vx", "vy", "vz", "ax_s", "ax_h", "id"):
-            assert np.array_equal(a[k], b[k]), k
+        if prec == 0:   # FP64: bitwise
+            for k in ("x", "y", "z", "vx", "vy", "vz", "ax_s", "ax_h", "id"):
+                assert np.array_equal(a[k], b[k]), k
+        else:           # FP32: chunked sums are added atomically, so equal to rounding
+            assert np.array_equal(a["id"], b["id"])
+            for k in ("x", "y", "z"):
+                assert np.max(np.abs(a[k] - b[k])) <= 1e-10
+            for w in ("s", "h"):
+                A = np.stack([a["a%s_%s" % (d, w)] for d in "xyz"], 1).astype(np.float64)
+                B = np.stack([b["a%s_%s" % (d, w)] for d in "xyz"], 1).astype(np.float64)
+                nz = np.linalg.norm(A, axis=1) > 0
+                e = np.linalg.norm(A - B, axis=1)[nz] / np.linalg.norm(A, axis=1)[nz]
+                assert np.percentile(e, 99) <= 1e-5
 
 
 def test_kick_drift_calls(H):
