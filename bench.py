@@ -252,7 +252,9 @@ def main():
     hard_ms, hard_n = ctx.hybrid_profile_read(1)
     walk_ms, walk_n = ctx.hybrid_profile_read(2)
     tree_ms, tree_n = ctx.hybrid_profile_read(3)
-    integ_ms, integ_n = ctx.hybrid_profile_read(4, reset=True)
+    integ_ms, integ_n = ctx.hybrid_profile_read(4)
+    sort_ms, topo_ms, mom_ms, grp_ms = (ctx.hybrid_profile_read(k)[0] for k in (5, 6, 7, 8))
+    ctx.hybrid_profile_read(0, reset=True)
     ctx.hybrid_profile(False)
     if dist:
         t = torch.tensor([t_steps], device="cuda")
@@ -324,7 +326,9 @@ def main():
             "force_err_rms_vs_direct": ferr,
             "kernel_ms_per_step": {"far_pair": soft_ms / args.steps, "near_pair": hard_ms / args.steps,
                                    "walk": walk_ms / args.steps, "tree_build": tree_ms / args.steps,
-                                   "kick_drift": integ_ms / args.steps},
+                                   "kick_drift": integ_ms / args.steps,
+                                   "tree_parts": {"sort": sort_ms / args.steps, "topology": topo_ms / args.steps,
+                                                  "moments": mom_ms / args.steps, "groups": grp_ms / args.steps}},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -57,7 +57,10 @@ typedef enum {
  * precision 0: all pair arithmetic in FP64; 1: FP32 pair arithmetic on
  *          coordinates relative to each sink group (state stays FP64)
  * mac      0: opening angle theta; 1: absolute MAC with a_err (Eq. 5-6)
- * threads_per_group, tile_depth: tuning knobs, 0 = built-in defaults */
+ * threads_per_group: lanes that share one copy of a sink group in the FP32
+ *          pair kernels; each lane then keeps ceil(n_crit / threads_per_group)
+ *          sinks (1, 2 or 4) in registers. 0 = built-in default.
+ * tile_depth: reserved tuning knob (0). */
 typedef struct {
     double G, eps, theta, R1, R2, dt_soft, a_err;
     int32_t n_hard, n_leaf, n_crit;
@@ -177,10 +180,11 @@ hybrid_status hybrid_lists_copy(hybrid_ctx *ctx, int64_t *counts, int64_t *entri
  * pairs, the hard force the near pairs. */
 hybrid_status hybrid_interactions(hybrid_ctx *ctx, int64_t *far, int64_t *near);
 
-/* Profiling: when enabled, the pair kernels are bracketed by CUDA events on
- * the context stream. hybrid_profile_read synchronises and returns, per
- * kernel kind (0 soft pair, 1 hard pair, 2 walk, 3 tree build, 4 kick/drift),
- * the summed milliseconds and launch count since the last reset. */
+/* Profiling: when enabled, each stage is bracketed by CUDA events on the
+ * context stream. hybrid_profile_read synchronises and returns, per kind
+ * (0 far pair kernel, 1 near pair kernel, 2 walk, 3 tree build, 4 kick/drift,
+ * 5 key sort, 6 tree topology, 7 moments, 8 groups; 5-8 are parts of 3), the
+ * summed milliseconds and number of brackets since the last reset. */
 hybrid_status hybrid_profile(hybrid_ctx *ctx, int enable);
 hybrid_status hybrid_profile_read(hybrid_ctx *ctx, int kind, double *ms, int64_t *launches, int reset);
 

@@ -80,7 +80,10 @@ struct SysIO {
     int64_t n, off;
 };
 
-enum ProfKind { PROF_SOFT = 0, PROF_HARD = 1, PROF_WALK = 2, PROF_TREE = 3, PROF_INTEG = 4, PROF_KINDS = 5 };
+enum ProfKind {
+    PROF_SOFT = 0, PROF_HARD = 1, PROF_WALK = 2, PROF_TREE = 3, PROF_INTEG = 4,
+    PROF_SORT = 5, PROF_TOPO = 6, PROF_MOM = 7, PROF_GROUPS = 8, PROF_KINDS = 9
+};
 
 }  // namespace hy
 
@@ -117,6 +120,8 @@ struct hybrid_ctx {
     // tree
     hy::Buf lvl, nfirst, ncount, nchild, nnch, nparent, nlevel, ndone, leafof;
     hy::Buf pc, pD, pn, rec, rb2d, rd2b, rhist;     // topology build scratch
+    hy::Buf nbig, mitems, mpart;                  // moments of large cells: chunk items and sums
+    int64_t capItems = 0;
     hy::Buf nM, ncx, ncy, ncz, nB2, nbmax;     // FP64 moments
     hy::Buf nA, nB, ncrit, ntopo;              // FP32 walk/pair node data
     hy::Buf nD, nrb, nhr;                      // FP64 walk/pair node data (precision 0)

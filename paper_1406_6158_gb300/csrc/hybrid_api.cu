@@ -147,7 +147,7 @@ bool alloc_nodes(hybrid_ctx *c, int64_t cap)
     for (Buf *b : {&c->nfirst, &c->ncount, &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->rb2d,
                    &c->rd2b})
         ok = ok && ensure(c, *b, n * 4);
-    ok = ok && ensure(c, c->rec, n * 8);
+    ok = ok && ensure(c, c->rec, n * 8) && ensure(c, c->nbig, n * 4);
     ok = ok && ensure(c, c->rhist, (size_t)(LEVELS + 1) * ((n + 1023) / 1024) * 4);
     for (Buf *b : {&c->nM, &c->ncx, &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nrb, &c->nhr, &c->ndelta, &c->nside})
         ok = ok && ensure(c, *b, n * 8);
@@ -177,6 +177,10 @@ bool reserve(hybrid_ctx *c)
         ok = ok && ensure(c, c->vals[0], n * 4) && ensure(c, c->vals[1], n * 4);
         ok = ok && ensure(c, c->gF, n * sizeof(GroupF)) && ensure(c, c->glo, n * 24) && ensure(c, c->ghi, n * 24);
         ok = ok && ensure(c, c->lcnt, (3 * n + 2) * 8) && ensure(c, c->wstart, (n + 2) * 4);
+        // chunks of 128 particles of the large cells: at most 2 N / 128 per level
+        const size_t items = 44 * n / 128 + 4096;
+        ok = ok && ensure(c, c->mitems, items * 4) && ensure(c, c->mpart, items * 40);
+        if (ok) c->capItems = (int64_t)items;
         if (ok) {
             c->capN = N;
             c->capGroups = N;
@@ -337,11 +341,20 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
     case OP_BUILD: {
         cudaEvent_t e0 = nullptr;
         prof_begin(c, PROF_TREE, &e0);
+        cudaEvent_t e1 = nullptr;
+        prof_begin(c, PROF_SORT, &e1);
         launch_box(c);
         launch_keys_sort_permute(c);
+        prof_end(c, PROF_SORT, e1);
+        prof_begin(c, PROF_TOPO, &e1);
         launch_build_levels(c);
+        prof_end(c, PROF_TOPO, e1);
+        prof_begin(c, PROF_MOM, &e1);
         launch_moments(c);
+        prof_end(c, PROF_MOM, e1);
+        prof_begin(c, PROF_GROUPS, &e1);
         launch_groups(c);
+        prof_end(c, PROF_GROUPS, e1);
         prof_end(c, PROF_TREE, e0);
         break;
     }
@@ -649,7 +662,7 @@ hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stre
         delete c;
         return HYBRID_ECUDA;
     }
-    c->walk_warps = c->nsm * 16;
+    c->walk_warps = c->nsm * 32;
     {   // HYBRID_GRAPHS=0 enqueues every op directly instead of replaying captured CUDA graphs
         const char *g = getenv("HYBRID_GRAPHS");
         if (g && g[0] == '0') c->use_graphs = false;
@@ -688,7 +701,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
                   &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
                   &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
                   &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,
-                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap};
+                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap, &c->nbig, &c->mitems, &c->mpart};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (int f = 0; f < 7; ++f) {

@@ -208,7 +208,18 @@ __device__ __forceinline__ void sweep(const PairArgs &a, uint64_t q0, uint64_t q
         __syncwarp();
         if (t0 + TILE < q1) fetch(t0 + TILE);   // next tile's loads overlap this tile's arithmetic
         if (active) {
-            for (int j = copy; j < nt; j += copies) {
+            int j = copy;
+            if (!NEAR) {   // two sources per round: one loop overhead per 2 KS interactions
+                for (; j + copies < nt; j += 2 * copies) {
+                    const float4 q0 = tile[j], q1 = tile[j + copies];
+#pragma unroll
+                    for (int k = 0; k < KS; ++k) {
+                        body_far<MODE == 1>(q0, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
+                        body_far<MODE == 1>(q1, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
+                    }
+                }
+            }
+            for (; j < nt; j += copies) {
                 const float4 q = tile[j];
                 if (!NEAR) {
 #pragma unroll
@@ -539,13 +550,19 @@ void fill_args(hybrid_ctx *c, PairArgs &a)
 template <int KS, bool NEAR, bool SOFT, bool HARD>
 void go_f32(hybrid_ctx *c, const PairArgs &a)
 {
-    k_pair_f32<KS, NEAR, SOFT, HARD><<<c->nsm * 12, PAIR_THREADS, 0, c->st>>>(a);
+    k_pair_f32<KS, NEAR, SOFT, HARD><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
 }
 
+// Sinks per lane KS = ceil(n_crit / threads_per_group), from 1 to 4; the
+// default is 4 for the far kernel (one shared-memory read feeds 4
+// interactions) and 2 for the near kernel (it also keeps hi/lo offsets per sink).
 template <bool NEAR, bool SOFT, bool HARD>
 void go_ks(hybrid_ctx *c, const PairArgs &a)
 {
-    const int ks = c->p.n_crit <= 32 ? 1 : (c->p.n_crit <= 64 ? 2 : 4);
+    int ks;
+    if (c->p.threads_per_group > 0) ks = (c->p.n_crit + c->p.threads_per_group - 1) / c->p.threads_per_group;
+    else ks = NEAR ? (c->p.n_crit > 64 ? 4 : 2) : 4;
+    ks = ks <= 1 ? 1 : (ks <= 2 ? 2 : 4);
     if (ks == 1) go_f32<1, NEAR, SOFT, HARD>(c, a);
     else if (ks == 2) go_f32<2, NEAR, SOFT, HARD>(c, a);
     else go_f32<4, NEAR, SOFT, HARD>(c, a);

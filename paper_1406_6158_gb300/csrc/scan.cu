@@ -126,10 +126,62 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(T *data, int64_t n_h
     }
 }
 
+// One block of 1024 threads scans the whole array (short arrays): chunks of
+// 1024 x IPT elements, a carry between chunks.
+constexpr int SMALL_IPT = 8;
+constexpr int64_t SMALL_MAX = 1024 * SMALL_IPT;   // one chunk: a single pass over the array
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_small(T *data, int64_t n_host, const int64_t *d_n, uint64_t *d_total,
+                                                     const Status *st)
+{
+    if (st && st->code) return;
+    const int64_t n = d_n ? *d_n : n_host;
+    __shared__ uint64_t wsum[32];
+    __shared__ uint64_t carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < n; b0 += 1024 * SMALL_IPT) {
+        const int64_t base = b0 + (int64_t)threadIdx.x * SMALL_IPT;
+        T v[SMALL_IPT];
+        uint64_t acc = 0;
+#pragma unroll
+        for (int k = 0; k < SMALL_IPT; ++k) {
+            v[k] = (base + k < n) ? data[base + k] : T(0);
+            acc += (uint64_t)v[k];
+        }
+        const uint64_t inc = warp_incl_scan(acc);
+        if (lane == 31) wsum[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            const uint64_t s = wsum[lane];
+            wsum[lane] = warp_incl_scan(s) - s;
+        }
+        __syncthreads();
+        const uint64_t c0 = carry;
+        uint64_t ex = c0 + wsum[w] + inc - acc;
+#pragma unroll
+        for (int k = 0; k < SMALL_IPT; ++k) {
+            if (base + k < n) data[base + k] = (T)ex;
+            ex += (uint64_t)v[k];
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = c0 + wsum[31] + inc;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && d_total) *d_total = carry;
+}
+
 template <typename T>
 static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,
                       bool always)
 {
+    if (n_max <= SMALL_MAX) {
+        k_scan_small<T><<<1, 1024, 0, c->st>>>(data, n_host, d_n, d_total, always ? nullptr : status_dev(c));
+        c->launches += 1;
+        return;
+    }
     const int64_t nseg_max = (n_max + SCAN_SEG - 1) / SCAN_SEG;
     if (nseg_max <= 0) {
         if (d_total) cudaMemsetAsync(d_total, 0, sizeof(uint64_t), c->st);

@@ -42,48 +42,45 @@ __global__ void __launch_bounds__(256) k_box(const double *__restrict__ x, const
                                              const Status *st)
 {
     (void)st;   // the sort always runs: later kernels rely on a consistent permutation
-    __shared__ double sh[6][8];
+    // min/max of the order-preserving integer images: exact, and no FP64 pipe work
+    __shared__ unsigned long long sh[6][8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunks[c];
-        double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        unsigned long long v[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
         for (int i = threadIdx.x; i < ch.len; i += blockDim.x) {
             const int64_t k = ch.start + i;
-            const double p0 = x[k], p1 = y[k], p2 = z[k];
-            v[0] = fmin(v[0], p0);
-            v[1] = fmin(v[1], p1);
-            v[2] = fmin(v[2], p2);
-            v[3] = fmax(v[3], p0);
-            v[4] = fmax(v[4], p1);
-            v[5] = fmax(v[5], p2);
+            const unsigned long long p0 = ord_dbl(x[k]), p1 = ord_dbl(y[k]), p2 = ord_dbl(z[k]);
+            v[0] = min(v[0], p0);
+            v[1] = min(v[1], p1);
+            v[2] = min(v[2], p2);
+            v[3] = max(v[3], p0);
+            v[4] = max(v[4], p1);
+            v[5] = max(v[5], p2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) v[j] = fmin(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+            for (int j = 0; j < 3; ++j) v[j] = min(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
 #pragma unroll
-            for (int j = 3; j < 6; ++j) v[j] = fmax(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+            for (int j = 3; j < 6; ++j) v[j] = max(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
         }
         if (lane == 0)
             for (int j = 0; j < 6; ++j) sh[j][w] = v[j];
         __syncthreads();
         if (threadIdx.x < 6) {
             const int j = threadIdx.x;
-            double r = sh[j][0];
-            for (int k = 1; k < 8; ++k) r = (j < 3) ? fmin(r, sh[j][k]) : fmax(r, sh[j][k]);
-            if (j < 3) atomicMin(&bmin[3 * ch.sys + j], ord_dbl(r));
-            else atomicMax(&bmax[3 * ch.sys + j - 3], ord_dbl(r));
+            unsigned long long r = sh[j][0];
+            for (int k = 1; k < 8; ++k) r = (j < 3) ? min(r, sh[j][k]) : max(r, sh[j][k]);
+            if (j < 3) atomicMin(&bmin[3 * ch.sys + j], r);
+            else atomicMax(&bmax[3 * ch.sys + j - 3], r);
         }
         __syncthreads();
     }
 }
 
-__global__ void k_box_final(int S, const unsigned long long *bmin, const unsigned long long *bmax, SysBox *box,
-                            const Status *st)
+__device__ __forceinline__ SysBox make_box(const unsigned long long *bmin, const unsigned long long *bmax, int s)
 {
-    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
     double lo[3], ext = 0.0;
     for (int d = 0; d < 3; ++d) {
         lo[d] = unord_dbl(bmin[3 * s + d]);
@@ -105,7 +102,7 @@ __global__ void k_box_final(int S, const unsigned long long *bmin, const unsigne
     b.u = ldexp(L, -20);
     b.inv_u = ldexp(1.0, 20) / L;
     b.pad = 0.0;
-    box[s] = b;
+    return b;
 }
 
 // ---------------------------------------------------------------------------
@@ -142,14 +139,23 @@ __device__ __forceinline__ void grid_split(double x, double lo0, const SysBox &b
     l = (float)__dsub_rn(xp, hh);
 }
 
+// Also finishes the root cubes (from the atomic min/max) and stores them.
 __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restrict__ x, const double *__restrict__ y,
-                                              const double *__restrict__ z, const int32_t *__restrict__ psys,
-                                              const SysBox *__restrict__ box, uint64_t *__restrict__ key,
-                                              uint32_t *__restrict__ val, const Status *st)
+                                              const double *__restrict__ z, const int32_t *__restrict__ psys, int S,
+                                              const unsigned long long *__restrict__ bmin,
+                                              const unsigned long long *__restrict__ bmax, SysBox *__restrict__ boxout,
+                                              uint64_t *__restrict__ key, uint32_t *__restrict__ val, const Status *st)
 {
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < S; s += blockDim.x) boxout[s] = make_box(bmin, bmax, s);
+    __shared__ SysBox b1;   // single-system batches: the cube computed once per block
+    if (S == 1) {
+        if (threadIdx.x == 0) b1 = make_box(bmin, bmax, 0);
+        __syncthreads();
+    }
     (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const SysBox b = box[psys[i]];
+        const SysBox b = S == 1 ? b1 : make_box(bmin, bmax, psys[i]);
         const uint32_t qx = cell_coord(x[i], b.lo[0], b.scale);
         const uint32_t qy = cell_coord(y[i], b.lo[1], b.scale);
         const uint32_t qz = cell_coord(z[i], b.lo[2], b.scale);
@@ -309,28 +315,20 @@ __global__ void __launch_bounds__(256) k_permute(PermArgs a, const Status *st)
 // gives each particle its slot), then stably sorted by level: the result is
 // the breadth-first order (level, system, key) of the split rule.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_prefix_c(int64_t N, const uint64_t *__restrict__ key,
-                                                  const int32_t *__restrict__ psys, int8_t *__restrict__ pc,
-                                                  const Status *st)
+// c(i): common leading octal digits of keys i-1 and i; -1 at a system's first particle
+__device__ __forceinline__ int prefix_c(const uint64_t *__restrict__ key, const int32_t *__restrict__ psys, int64_t i)
 {
-    if (st->code) return;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        int c;
-        if (i == 0 || psys[i] != psys[i - 1]) {
-            c = -1;
-        } else {
-            const unsigned long long x = key[i - 1] ^ key[i];
-            c = x == 0ull ? LEVELS : (__clzll((long long)x) - 1) / 3;   // keys use bits 0..62
-        }
-        pc[i] = (int8_t)c;
-    }
+    if (i == 0 || psys[i] != psys[i - 1]) return -1;
+    const unsigned long long x = key[i - 1] ^ key[i];
+    return x == 0ull ? LEVELS : (__clzll((long long)x) - 1) / 3;   // keys use bits 0..62
 }
 
 constexpr int LD_T = 256;
 
 // Leaf depth D(p) and the number of nodes particle p starts, max(0, D - c).
-__global__ void __launch_bounds__(LD_T) k_leaf_depth(int64_t N, const int8_t *__restrict__ pc, int n_leaf,
-                                                     uint8_t *__restrict__ pD, uint32_t *__restrict__ pn,
+__global__ void __launch_bounds__(LD_T) k_leaf_depth(int64_t N, const uint64_t *__restrict__ key,
+                                                     const int32_t *__restrict__ psys, int8_t *__restrict__ pc,
+                                                     int n_leaf, uint8_t *__restrict__ pD, uint32_t *__restrict__ pn,
                                                      const Status *st)
 {
     if (st->code) return;
@@ -340,7 +338,9 @@ __global__ void __launch_bounds__(LD_T) k_leaf_depth(int64_t N, const int8_t *__
         __syncthreads();
         for (int k = threadIdx.x; k < win; k += blockDim.x) {
             const int64_t j = base - n_leaf + k;
-            sc[k] = (j < 0 || j >= N) ? (int8_t)-1 : pc[j];
+            const int cj = (j < 0 || j >= N) ? -1 : prefix_c(key, psys, j);
+            sc[k] = (int8_t)cj;
+            if (k >= n_leaf && k < n_leaf + LD_T && j < N) pc[j] = (int8_t)cj;
         }
         __syncthreads();
         const int64_t p = base + threadIdx.x;
@@ -564,6 +564,7 @@ struct MomArgs {
     double *M, *cx, *cy, *cz, *B2;
     float4 *nA, *nB;
     uint32_t *done, *leafof;
+    const float4 *phi, *plo;
 };
 
 __device__ __forceinline__ uint32_t digit_at(uint64_t key, int lev)
@@ -603,78 +604,179 @@ __device__ __forceinline__ void store_com(const MomArgs &a, uint32_t c, double M
     a.nB[c] = make_float4(l[0], l[1], l[2], 0.0f);
 }
 
-__device__ __forceinline__ void com_or_centre(const MomArgs &a, uint32_t c, double M, double t0, double t1,
-                                              double t2, double &p0, double &p1, double &p2)
+// Moments straight from each cell's particle range, with no wait on the
+// children: M, sum m (x - o) and Q = sum m |x - o|^2 with o = the cell's first
+// particle; COM = o + sum m (x - o) / M and B2 = Q - M |COM - o|^2 (o lies
+// inside the cell, so the subtraction loses little). Cells of at most MOM_CH
+// particles: one warp each (at most 4 rounds of loads per lane). Larger cells: chunks of MOM_CH particles, one warp
+// per chunk, then one warp per cell adds the chunk sums in chunk order.
+constexpr uint32_t MOM_CH = 128;
+
+struct MomSums {
+    double M, sx, sy, sz, Q;
+};
+
+// FP32 form: offsets from the first particle from the hi/lo copies (hi parts
+// on a common grid, so hi_i - hi_f is exact), sums of at most MOM_CH terms in
+// FP32; the chunk sums of larger cells are added in FP64.
+__device__ __forceinline__ MomSums mom_range_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
+                                                 uint32_t f, uint32_t n, uint32_t ref, int lane)
 {
-    if (M > 0.0) {
-        p0 = t0 / M;
-        p1 = t1 / M;
-        p2 = t2 / M;
+    const float4 hr = phi[ref], lr = plo[ref];
+    float M = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f, Q = 0.0f;
+#pragma unroll 4
+    for (uint32_t i = f + lane; i < f + n; i += 32) {
+        const float4 h = phi[i], l = plo[i];
+        const float d0 = (h.x - hr.x) + (l.x - lr.x), d1 = (h.y - hr.y) + (l.y - lr.y), d2 = (h.z - hr.z) + (l.z - lr.z);
+        const float mi = h.w;
+        M += mi;
+        sx = fmaf(mi, d0, sx);
+        sy = fmaf(mi, d1, sy);
+        sz = fmaf(mi, d2, sz);
+        Q = fmaf(mi, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), Q);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        M += __shfl_xor_sync(0xffffffffu, M, o);
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        Q += __shfl_xor_sync(0xffffffffu, Q, o);
+    }
+    MomSums r = {(double)M, (double)sx, (double)sy, (double)sz, (double)Q};
+    return r;
+}
+
+__device__ __forceinline__ MomSums mom_range(const MomArgs &a, uint32_t f, uint32_t n, double o0, double o1, double o2,
+                                             int lane)
+{
+    MomSums r = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (uint32_t i = f + lane; i < f + n; i += 32) {
+        const double mi = a.m[i];
+        const double d0 = a.x[i] - o0, d1 = a.y[i] - o1, d2 = a.z[i] - o2;
+        r.M += mi;
+        r.sx += mi * d0;
+        r.sy += mi * d1;
+        r.sz += mi * d2;
+        r.Q += mi * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // fixed butterfly: the same order every run
+        r.M += __shfl_xor_sync(0xffffffffu, r.M, o);
+        r.sx += __shfl_xor_sync(0xffffffffu, r.sx, o);
+        r.sy += __shfl_xor_sync(0xffffffffu, r.sy, o);
+        r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
+        r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void mom_store(const MomArgs &a, uint32_t c, const MomSums &r, double o0, double o1,
+                                          double o2)
+{
+    double c0, c1, c2, B2 = 0.0;
+    if (r.M > 0.0) {
+        const double e0 = r.sx / r.M, e1 = r.sy / r.M, e2 = r.sz / r.M;
+        c0 = o0 + e0;
+        c1 = o1 + e1;
+        c2 = o2 + e2;
+        B2 = fmax(r.Q - r.M * (e0 * e0 + e1 * e1 + e2 * e2), 0.0);
     } else {   // massless cell: its geometric centre
         double o[3], sd;
         const uint32_t f = a.nfirst[c];
         cell_geom(a.box[a.psys[f]], a.key[f], a.nlevel[c], o, &sd);
-        p0 = o[0] + 0.5 * sd;
-        p1 = o[1] + 0.5 * sd;
-        p2 = o[2] + 0.5 * sd;
+        c0 = o[0] + 0.5 * sd;
+        c1 = o[1] + 0.5 * sd;
+        c2 = o[2] + 0.5 * sd;
     }
+    store_com(a, c, r.M, c0, c1, c2, B2);
 }
 
-// leaves: sums over their particles
-__global__ void __launch_bounds__(256) k_mom_leaves(MomArgs a, const Status *st)
+// every cell: small ones finished here, large ones get their chunk items
+template <bool F64>
+__global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long *nitems, uint32_t *bigbase,
+                                                   uint32_t *items, uint32_t cap_items, Status *st, int where)
 {
     if (st->code) return;
     const uint32_t total = a.lvl[LEVELS + 1];
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
-        if (a.nnch[c] != 0) continue;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
         const uint32_t f = a.nfirst[c], n = a.ncount[c];
-        double M = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (uint32_t i = f; i < f + n; ++i) {
-            const double mi = a.m[i];
-            M += mi;
-            s0 += mi * a.x[i];
-            s1 += mi * a.y[i];
-            s2 += mi * a.z[i];
-            a.leafof[i] = c;
+        const bool leaf = a.nnch[c] == 0;
+        if (n <= MOM_CH) {
+            if (leaf)
+                for (uint32_t i = f + lane; i < f + n; i += 32) a.leafof[i] = c;
+            const double o0 = a.x[f], o1 = a.y[f], o2 = a.z[f];
+            const MomSums r = F64 ? mom_range(a, f, n, o0, o1, o2, lane) : mom_range_f32(a.phi, a.plo, f, n, f, lane);
+            if (lane == 0) mom_store(a, c, r, o0, o1, o2);
+        } else if (lane == 0) {
+            const uint32_t nch = (n + MOM_CH - 1) / MOM_CH;
+            const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
+            if (base + nch > cap_items) {
+                fail(st, HYBRID_ECAPACITY, where);
+                continue;
+            }
+            bigbase[c] = (uint32_t)base;
+            for (uint32_t k = 0; k < nch; ++k) items[base + k] = c;
         }
-        double c0, c1, c2;
-        com_or_centre(a, c, M, s0, s1, s2, c0, c1, c2);
-        double B2 = 0.0;
-        for (uint32_t i = f; i < f + n; ++i) {
-            const double d0 = a.x[i] - c0, d1 = a.y[i] - c1, d2 = a.z[i] - c2;
-            B2 += a.m[i] * (d0 * d0 + d1 * d1 + d2 * d2);
-        }
-        store_com(a, c, M, c0, c1, c2, B2);
     }
 }
 
-// internal nodes of one level: sums over their children (done by the
-// previous launch); B2 by the parallel-axis rule
-__global__ void __launch_bounds__(256) k_mom_level(int lev, MomArgs a, const Status *st)
+// chunk sums of large cells
+template <bool F64>
+__global__ void __launch_bounds__(256) k_mom_chunks(MomArgs a, const unsigned long long *nitems,
+                                                    const uint32_t *bigbase, const uint32_t *items,
+                                                    MomSums *partial, const Status *st)
 {
     if (st->code) return;
-    const uint32_t l0 = a.lvl[lev], l1 = a.lvl[lev + 1];
-    for (uint32_t p = l0 + blockIdx.x * blockDim.x + threadIdx.x; p < l1; p += gridDim.x * blockDim.x) {
-        const uint32_t k = a.nnch[p];
-        if (k == 0) continue;
-        const uint32_t ch = a.nchild[p];
-        double Mp = 0.0, t0 = 0.0, t1 = 0.0, t2 = 0.0;
-        for (uint32_t j = 0; j < k; ++j) {
-            const double Mj = a.M[ch + j];
-            Mp += Mj;
-            t0 += Mj * a.cx[ch + j];
-            t1 += Mj * a.cy[ch + j];
-            t2 += Mj * a.cz[ch + j];
+    const uint32_t T = (uint32_t)*nitems;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < T; w += nw) {
+        const uint32_t c = items[w];
+        const uint32_t k = w - bigbase[c];
+        const uint32_t f = a.nfirst[c], n = a.ncount[c];
+        const uint32_t f0 = f + k * MOM_CH, n0 = min(MOM_CH, f + n - f0);
+        if (a.nnch[c] == 0)
+            for (uint32_t i = f0 + lane; i < f0 + n0; i += 32) a.leafof[i] = c;
+        const MomSums r =
+            F64 ? mom_range(a, f0, n0, a.x[f], a.y[f], a.z[f], lane) : mom_range_f32(a.phi, a.plo, f0, n0, f, lane);
+        if (lane == 0) partial[w] = r;
+    }
+}
+
+// large cells: chunk sums added in chunk order
+__global__ void __launch_bounds__(256) k_mom_big(MomArgs a, const uint32_t *bigbase, const MomSums *partial,
+                                                 const Status *st)
+{
+    if (st->code) return;
+    const uint32_t total = a.lvl[LEVELS + 1];
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+        const uint32_t f = a.nfirst[c], n = a.ncount[c];
+        if (n <= MOM_CH) continue;
+        const uint32_t nch = (n + MOM_CH - 1) / MOM_CH, b0 = bigbase[c];
+        MomSums r = {0.0, 0.0, 0.0, 0.0, 0.0};
+        for (uint32_t k = lane; k < nch; k += 32) {
+            const MomSums q = partial[b0 + k];
+            r.M += q.M;
+            r.sx += q.sx;
+            r.sy += q.sy;
+            r.sz += q.sz;
+            r.Q += q.Q;
         }
-        double p0, p1, p2;
-        com_or_centre(a, p, Mp, t0, t1, t2, p0, p1, p2);
-        double Bp = 0.0;
-        for (uint32_t j = 0; j < k; ++j) {
-            const double Mj = a.M[ch + j];
-            const double d0 = a.cx[ch + j] - p0, d1 = a.cy[ch + j] - p1, d2 = a.cz[ch + j] - p2;
-            Bp += a.B2[ch + j] + Mj * (d0 * d0 + d1 * d1 + d2 * d2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            r.M += __shfl_xor_sync(0xffffffffu, r.M, o);
+            r.sx += __shfl_xor_sync(0xffffffffu, r.sx, o);
+            r.sy += __shfl_xor_sync(0xffffffffu, r.sy, o);
+            r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
+            r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
         }
-        store_com(a, p, Mp, p0, p1, p2, Bp);
+        if (lane == 0) mom_store(a, c, r, a.x[f], a.y[f], a.z[f]);
     }
 }
 
@@ -862,24 +964,27 @@ __global__ void __launch_bounds__(256) k_group_box(const int64_t *__restrict__ n
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
         const uint32_t f = gfirst[g], n = gcount[g];
-        double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+        // exact min/max through the order-preserving integer images (no FP64 pipe work)
+        unsigned long long u[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
         for (uint32_t i = f + lane; i < f + n; i += 32) {
-            const double p0 = x[i], p1 = y[i], p2 = z[i];
-            v[0] = fmin(v[0], p0);
-            v[1] = fmin(v[1], p1);
-            v[2] = fmin(v[2], p2);
-            v[3] = fmax(v[3], p0);
-            v[4] = fmax(v[4], p1);
-            v[5] = fmax(v[5], p2);
+            const unsigned long long p0 = ord_dbl(x[i]), p1 = ord_dbl(y[i]), p2 = ord_dbl(z[i]);
+            u[0] = min(u[0], p0);
+            u[1] = min(u[1], p1);
+            u[2] = min(u[2], p2);
+            u[3] = max(u[3], p0);
+            u[4] = max(u[4], p1);
+            u[5] = max(u[5], p2);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int j = 0; j < 3; ++j) v[j] = fmin(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+            for (int j = 0; j < 3; ++j) u[j] = min(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
 #pragma unroll
-            for (int j = 3; j < 6; ++j) v[j] = fmax(v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+            for (int j = 3; j < 6; ++j) u[j] = max(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
         }
         if (lane == 0) {
+            double v[6];
+            for (int j = 0; j < 6; ++j) v[j] = unord_dbl(u[j]);
             const SysBox b = box[psys[f]];
             float hc[3], lc[3], he[3];
             for (int d = 0; d < 3; ++d) {
@@ -919,9 +1024,7 @@ void launch_box(hybrid_ctx *c)
     k_box<<<std::min(c->nchunks, c->nsm * 16), 256, 0, c->st>>>(
         (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const Chunk *)c->chunks_dev.p,
         c->nchunks, (unsigned long long *)c->boxmin.p, (unsigned long long *)c->boxmax.p, st);
-    k_box_final<<<(c->S + 127) / 128, 128, 0, c->st>>>(c->S, (const unsigned long long *)c->boxmin.p,
-                                                       (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, st);
-    c->launches += 2;
+    c->launches += 1;
 }
 
 void launch_keys_sort_permute(hybrid_ctx *c)
@@ -931,8 +1034,10 @@ void launch_keys_sort_permute(hybrid_ctx *c)
     uint64_t *k0 = (uint64_t *)c->keys[0].p, *k1 = (uint64_t *)c->keys[1].p;
     uint32_t *v0 = (uint32_t *)c->vals[0].p, *v1 = (uint32_t *)c->vals[1].p;
     k_keys<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const double *)c->x[0].p, (const double *)c->x[1].p,
-                                                    (const double *)c->x[2].p, (const int32_t *)c->psys.p,
-                                                    (const SysBox *)c->box.p, k0, v0, st);
+                                                    (const double *)c->x[2].p, (const int32_t *)c->psys.p, c->S,
+                                                    (const unsigned long long *)c->boxmin.p,
+                                                    (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0,
+                                                    st);
     c->launches++;
     const int grid = std::min(c->nchunks, c->nsm * 8);
     uint32_t *hist = (uint32_t *)c->hist.p;
@@ -987,9 +1092,9 @@ bool launch_build_levels(hybrid_ctx *c)
     uint32_t *pn = (uint32_t *)c->pn.p;
     const uint64_t *keys = (const uint64_t *)c->keys[0].p;
     uint64_t *d_tot = (uint64_t *)((char *)c->lvl.p + 256);
-    k_prefix_c<<<gridN, 256, 0, c->st>>>(N, keys, (const int32_t *)c->psys.p, pc, st);
     const size_t shm = (size_t)(LD_T + 2 * c->p.n_leaf);
-    k_leaf_depth<<<grid_for(c, N, LD_T, 8), LD_T, shm, c->st>>>(N, pc, c->p.n_leaf, pD, pn, st);
+    k_leaf_depth<<<grid_for(c, N, LD_T, 8), LD_T, shm, c->st>>>(N, keys, (const int32_t *)c->psys.p, pc,
+                                                                c->p.n_leaf, pD, pn, st);
     scan_u32(c, pn, N, nullptr, N, d_tot);
     unsigned long long *rec = (unsigned long long *)c->rec.p;
     k_records<<<gridN, 256, 0, c->st>>>(N, pc, pD, pn, d_tot, c->capNodes, rec, st, c->op);
@@ -1008,7 +1113,7 @@ bool launch_build_levels(hybrid_ctx *c)
     k_nodes_b<<<gridT, 256, 0, c->st>>>(d_tot, lvl, (const uint32_t *)c->nfirst.p, (const uint32_t *)c->ncount.p,
                                         (const uint32_t *)c->nlevel.p, (const uint32_t *)c->nchild.p,
                                         (uint32_t *)c->nnch.p, (uint32_t *)c->nparent.p, st);
-    c->launches += 8;
+    c->launches += 7;
     return true;
 }
 
@@ -1041,10 +1146,24 @@ void launch_moments(hybrid_ctx *c)
     a.nB = (float4 *)c->nB.p;
     a.done = (uint32_t *)c->ndone.p;
     a.leafof = (uint32_t *)c->leafof.p;
-    k_mom_leaves<<<grid, 256, 0, c->st>>>(a, st);
-    const int gridl = grid_for(c, c->N / 4 + 1024, 256, 4);
-    for (int lev = LEVELS - 1; lev >= 0; --lev) k_mom_level<<<gridl, 256, 0, c->st>>>(lev, a, st);
-    c->launches += LEVELS;
+    unsigned long long *nitems = (unsigned long long *)c->counter.p + 9;
+    cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), c->st);
+    const int gridw = grid_for(c, c->capNodes * 32, 256, 16);
+    a.phi = (const float4 *)c->phi.p;
+    a.plo = (const float4 *)c->plo.p;
+    if (c->p.precision == 0) {
+        k_mom_small<true><<<gridw, 256, 0, c->st>>>(a, nitems, (uint32_t *)c->nbig.p, (uint32_t *)c->mitems.p,
+                                                    (uint32_t)c->capItems, st, c->op);
+        k_mom_chunks<true><<<gridw, 256, 0, c->st>>>(a, nitems, (const uint32_t *)c->nbig.p,
+                                                     (const uint32_t *)c->mitems.p, (MomSums *)c->mpart.p, st);
+    } else {
+        k_mom_small<false><<<gridw, 256, 0, c->st>>>(a, nitems, (uint32_t *)c->nbig.p, (uint32_t *)c->mitems.p,
+                                                     (uint32_t)c->capItems, st, c->op);
+        k_mom_chunks<false><<<gridw, 256, 0, c->st>>>(a, nitems, (const uint32_t *)c->nbig.p,
+                                                      (const uint32_t *)c->mitems.p, (MomSums *)c->mpart.p, st);
+    }
+    k_mom_big<<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
+    c->launches += 2;
     const int gridp = grid_for(c, c->N, 256, 8);
     if (c->p.precision == 0)
         k_bmax<true><<<gridp, 256, 0, c->st>>>(
