@@ -40,7 +40,7 @@ struct SysBox {
     double L;
     double scale;
     double u, inv_u;
-    double pad;
+    float uf, inv_uf;   // u and 1/u in FP32 (powers of two: exact)
 };
 
 // Device status block: first failure wins (atomicCAS on code).
@@ -121,6 +121,7 @@ struct hybrid_ctx {
     hy::Buf lvl, nfirst, ncount, nchild, nnch, nparent, nlevel, ndone, leafof;
     hy::Buf pc, pD, pn, rec, rb2d, rd2b, rhist;     // topology build scratch
     hy::Buf nbig, mitems, mpart;                  // moments of large cells: chunk items and sums
+    hy::Buf nbmax32;                              // b_max as FP32 bits (FP32 form)
     int64_t capItems = 0;
     hy::Buf nM, ncx, ncy, ncz, nB2, nbmax;     // FP64 moments
     hy::Buf nA, nB, ncrit, ntopo;              // FP32 walk/pair node data

@@ -147,7 +147,7 @@ bool alloc_nodes(hybrid_ctx *c, int64_t cap)
     for (Buf *b : {&c->nfirst, &c->ncount, &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->rb2d,
                    &c->rd2b})
         ok = ok && ensure(c, *b, n * 4);
-    ok = ok && ensure(c, c->rec, n * 8) && ensure(c, c->nbig, n * 4);
+    ok = ok && ensure(c, c->rec, n * 8) && ensure(c, c->nbig, n * 4) && ensure(c, c->nbmax32, n * 4);
     ok = ok && ensure(c, c->rhist, (size_t)(LEVELS + 1) * ((n + 1023) / 1024) * 4);
     for (Buf *b : {&c->nM, &c->ncx, &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nrb, &c->nhr, &c->ndelta, &c->nside})
         ok = ok && ensure(c, *b, n * 8);
@@ -701,7 +701,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
                   &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
                   &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
                   &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,
-                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap, &c->nbig, &c->mitems, &c->mpart};
+                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap, &c->nbig, &c->mitems, &c->mpart, &c->nbmax32};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (int f = 0; f < 7; ++f) {

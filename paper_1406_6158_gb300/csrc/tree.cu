@@ -10,6 +10,7 @@
 #include "hy_internal.cuh"
 
 #include <cstdio>
+#include <type_traits>
 
 namespace hy {
 
@@ -101,7 +102,8 @@ __device__ __forceinline__ SysBox make_box(const unsigned long long *bmin, const
     b.scale = ldexp(1.0, LEVELS) / L;   // ratio of powers of two: exact
     b.u = ldexp(L, -20);
     b.inv_u = ldexp(1.0, 20) / L;
-    b.pad = 0.0;
+    b.uf = (float)b.u;
+    b.inv_uf = (float)b.inv_u;
     return b;
 }
 
@@ -619,32 +621,68 @@ struct MomSums {
 // FP32 form: offsets from the first particle from the hi/lo copies (hi parts
 // on a common grid, so hi_i - hi_f is exact), sums of at most MOM_CH terms in
 // FP32; the chunk sums of larger cells are added in FP64.
-__device__ __forceinline__ MomSums mom_range_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-                                                 uint32_t f, uint32_t n, uint32_t ref, int lane)
+struct MomSumsF {
+    float M, sx, sy, sz, Q;
+};
+
+__device__ __forceinline__ MomSumsF mom_range_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
+                                                  uint32_t f, uint32_t n, uint32_t ref, int lane)
 {
     const float4 hr = phi[ref], lr = plo[ref];
-    float M = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f, Q = 0.0f;
+    MomSumsF r = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
     for (uint32_t i = f + lane; i < f + n; i += 32) {
         const float4 h = phi[i], l = plo[i];
         const float d0 = (h.x - hr.x) + (l.x - lr.x), d1 = (h.y - hr.y) + (l.y - lr.y), d2 = (h.z - hr.z) + (l.z - lr.z);
         const float mi = h.w;
-        M += mi;
-        sx = fmaf(mi, d0, sx);
-        sy = fmaf(mi, d1, sy);
-        sz = fmaf(mi, d2, sz);
-        Q = fmaf(mi, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), Q);
+        r.M += mi;
+        r.sx = fmaf(mi, d0, r.sx);
+        r.sy = fmaf(mi, d1, r.sy);
+        r.sz = fmaf(mi, d2, r.sz);
+        r.Q = fmaf(mi, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), r.Q);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        M += __shfl_xor_sync(0xffffffffu, M, o);
-        sx += __shfl_xor_sync(0xffffffffu, sx, o);
-        sy += __shfl_xor_sync(0xffffffffu, sy, o);
-        sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        Q += __shfl_xor_sync(0xffffffffu, Q, o);
+        r.M += __shfl_xor_sync(0xffffffffu, r.M, o);
+        r.sx += __shfl_xor_sync(0xffffffffu, r.sx, o);
+        r.sy += __shfl_xor_sync(0xffffffffu, r.sy, o);
+        r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
+        r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
     }
-    MomSums r = {(double)M, (double)sx, (double)sy, (double)sz, (double)Q};
     return r;
+}
+
+// FP32 form: centre of mass as offsets e from the first particle f, stored
+// as the grid-aligned hi/lo pair; B2 goes to nB.w. No FP64 instruction here:
+// a single-lane FP64 instruction costs a full warp's FP64 pipe time.
+__device__ __forceinline__ void mom_store_f32(const MomArgs &a, uint32_t c, uint32_t f, float M, float e0, float e1,
+                                              float e2, float B2)
+{
+    const SysBox &b = a.box[a.psys[f]];
+    const float4 h = a.phi[f], l = a.plo[f];
+    const float t0 = l.x + e0, t1 = l.y + e1, t2 = l.z + e2;
+    const float g0 = rintf(t0 * b.inv_uf) * b.uf, g1 = rintf(t1 * b.inv_uf) * b.uf, g2 = rintf(t2 * b.inv_uf) * b.uf;
+    a.nA[c] = make_float4(h.x + g0, h.y + g1, h.z + g2, M);
+    a.nB[c] = make_float4(t0 - g0, t1 - g1, t2 - g2, B2);
+}
+
+// B2 of a small cell about its centre of mass e (offsets from particle ref),
+// summed directly so that no M|e|^2 cancels against the second moment.
+__device__ __forceinline__ float mom_b2_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
+                                            uint32_t f, uint32_t n, uint32_t ref, float e0, float e1, float e2,
+                                            int lane)
+{
+    const float4 hr = phi[ref], lr = plo[ref];
+    float q = 0.0f;
+    for (uint32_t i = f + lane; i < f + n; i += 32) {
+        const float4 h = phi[i], l = plo[i];
+        const float d0 = ((h.x - hr.x) + (l.x - lr.x)) - e0, d1 = ((h.y - hr.y) + (l.y - lr.y)) - e1,
+                    d2 = ((h.z - hr.z) + (l.z - lr.z)) - e2;
+        q = fmaf(h.w, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), q);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    return q;
 }
 
 __device__ __forceinline__ MomSums mom_range(const MomArgs &a, uint32_t f, uint32_t n, double o0, double o1, double o2,
@@ -708,9 +746,17 @@ __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long
         if (n <= MOM_CH) {
             if (leaf)
                 for (uint32_t i = f + lane; i < f + n; i += 32) a.leafof[i] = c;
-            const double o0 = a.x[f], o1 = a.y[f], o2 = a.z[f];
-            const MomSums r = F64 ? mom_range(a, f, n, o0, o1, o2, lane) : mom_range_f32(a.phi, a.plo, f, n, f, lane);
-            if (lane == 0) mom_store(a, c, r, o0, o1, o2);
+            if (F64) {
+                const double o0 = a.x[f], o1 = a.y[f], o2 = a.z[f];
+                const MomSums r = mom_range(a, f, n, o0, o1, o2, lane);
+                if (lane == 0) mom_store(a, c, r, o0, o1, o2);
+            } else {
+                const MomSumsF r = mom_range_f32(a.phi, a.plo, f, n, f, lane);
+                const float iM = r.M > 0.0f ? 1.0f / r.M : 0.0f;
+                const float e0 = r.sx * iM, e1 = r.sy * iM, e2 = r.sz * iM;
+                const float B2 = mom_b2_f32(a.phi, a.plo, f, n, f, e0, e1, e2, lane);
+                if (lane == 0) mom_store_f32(a, c, f, r.M, e0, e1, e2, B2);
+            }
         } else if (lane == 0) {
             const uint32_t nch = (n + MOM_CH - 1) / MOM_CH;
             const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
@@ -741,13 +787,23 @@ __global__ void __launch_bounds__(256) k_mom_chunks(MomArgs a, const unsigned lo
         const uint32_t f0 = f + k * MOM_CH, n0 = min(MOM_CH, f + n - f0);
         if (a.nnch[c] == 0)
             for (uint32_t i = f0 + lane; i < f0 + n0; i += 32) a.leafof[i] = c;
-        const MomSums r =
-            F64 ? mom_range(a, f0, n0, a.x[f], a.y[f], a.z[f], lane) : mom_range_f32(a.phi, a.plo, f0, n0, f, lane);
+        MomSums r;
+        if (F64) {
+            r = mom_range(a, f0, n0, a.x[f], a.y[f], a.z[f], lane);
+        } else {
+            const MomSumsF q = mom_range_f32(a.phi, a.plo, f0, n0, f, lane);
+            r.M = q.M;
+            r.sx = q.sx;
+            r.sy = q.sy;
+            r.sz = q.sz;
+            r.Q = q.Q;
+        }
         if (lane == 0) partial[w] = r;
     }
 }
 
 // large cells: chunk sums added in chunk order
+template <bool F64>
 __global__ void __launch_bounds__(256) k_mom_big(MomArgs a, const uint32_t *bigbase, const MomSums *partial,
                                                  const Status *st)
 {
@@ -776,7 +832,20 @@ __global__ void __launch_bounds__(256) k_mom_big(MomArgs a, const uint32_t *bigb
             r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
             r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
         }
-        if (lane == 0) mom_store(a, c, r, a.x[f], a.y[f], a.z[f]);
+        if (lane == 0) {
+            if (F64) mom_store(a, c, r, a.x[f], a.y[f], a.z[f]);
+            else {
+                // few large cells: finish in FP64 (parallel-axis form), store in FP32
+                double e0 = 0.0, e1 = 0.0, e2 = 0.0, B2 = 0.0;
+                if (r.M > 0.0) {
+                    e0 = r.sx / r.M;
+                    e1 = r.sy / r.M;
+                    e2 = r.sz / r.M;
+                    B2 = fmax(r.Q - r.M * (e0 * e0 + e1 * e1 + e2 * e2), 0.0);
+                }
+                mom_store_f32(a, c, f, (float)r.M, (float)e0, (float)e1, (float)e2, (float)B2);
+            }
+        }
     }
 }
 
@@ -793,8 +862,9 @@ __global__ void __launch_bounds__(256) k_bmax(int64_t N, const uint32_t *__restr
                                               const double *__restrict__ cz, const float4 *__restrict__ phi,
                                               const float4 *__restrict__ plo, const float4 *__restrict__ nA,
                                               const float4 *__restrict__ nB, unsigned long long *bmax,
-                                              const Status *st)
+                                              unsigned int *bmax32, const Status *st)
 {
+    using T = typename std::conditional<F64, double, float>::type;
     if (st->code) return;
     const int lane = threadIdx.x & 31;
     const int64_t nwarp_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -820,29 +890,31 @@ __global__ void __launch_bounds__(256) k_bmax(int64_t N, const uint32_t *__restr
         }
         for (int L = maxlev; L >= 0; --L) {
             const bool act = (lev == L);
-            double dist = 0.0;
+            T dist = T(0);
             if (act) {
                 if (F64) {
                     const double d0 = px - cx[c], d1 = py - cy[c], d2 = pz - cz[c];
-                    dist = sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                    dist = (T)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
                 } else {
                     const float4 A = nA[c], B = nB[c];
                     const float d0 = (ph.x - A.x) + (pl.x - B.x);
                     const float d1 = (ph.y - A.y) + (pl.y - B.y);
                     const float d2 = (ph.z - A.z) + (pl.z - B.z);
-                    dist = (double)sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+                    dist = (T)sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
                 }
             }
             const uint32_t keyv = act ? c : NONE;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const double du = __shfl_up_sync(0xffffffffu, dist, o);
+                const T du = __shfl_up_sync(0xffffffffu, dist, o);
                 const uint32_t ku = __shfl_up_sync(0xffffffffu, keyv, o);
-                if (lane >= o && ku == keyv) dist = fmax(dist, du);
+                if (lane >= o && ku == keyv) dist = dist > du ? dist : du;
             }
             const uint32_t kd = __shfl_down_sync(0xffffffffu, keyv, 1);
-            if (act && (lane == 31 || kd != keyv))
-                atomicMax(&bmax[c], (unsigned long long)__double_as_longlong(dist));
+            if (act && (lane == 31 || kd != keyv)) {
+                if (F64) atomicMax(&bmax[c], (unsigned long long)__double_as_longlong((double)dist));
+                else atomicMax(&bmax32[c], __float_as_uint((float)dist));   // non-negative: bit order = value order
+            }
             if (act) {
                 c = nparent[c];
                 lev = L - 1;
@@ -858,14 +930,32 @@ struct FinArgs {
     const int32_t *psys;
     const SysBox *box;
     const SysParams *sp;
-    const double *M, *cx, *cy, *cz, *B2;
-    const unsigned long long *bmax;
+    double *M, *cx, *cy, *cz, *B2;
+    unsigned long long *bmax;
+    const unsigned int *bmax32;
+    const float4 *nA, *nB;
     float2 *crit;
     uint4 *topo;
     double4_32a *nD;
     double *rb, *hr, *delta, *side, *org;
 };
 
+__device__ __forceinline__ void prefix_q(uint64_t key, uint32_t lev, uint32_t q[3])
+{
+    q[0] = q[1] = q[2] = 0;
+    for (uint32_t l = 1; l <= lev; ++l) {
+        const uint32_t d = digit_at(key, (int)l);
+        q[0] = (q[0] << 1) | ((d >> 2) & 1u);
+        q[1] = (q[1] << 1) | ((d >> 1) & 1u);
+        q[2] = (q[2] << 1) | (d & 1u);
+    }
+}
+
+// Per node: geometry, delta, MAC radius, walk criteria and packed topology.
+// F64: from the FP64 moments. FP32 form: delta, r_b and the criteria in FP32
+// from the hi/lo centre of mass (cell centres are exact in FP32 on the hi
+// grid), then the FP64 copies of the moments for inspection.
+template <bool F64>
 __global__ void __launch_bounds__(256) k_finalize(FinArgs a, const Status *st)
 {
     if (st->code) return;
@@ -873,29 +963,63 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a, const Status *st)
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < total; c += gridDim.x * blockDim.x) {
         const uint32_t f = a.nfirst[c];
         const int s = a.psys[f];
-        const SysParams P = a.sp[s];
-        double o[3], sd;
-        cell_geom(a.box[s], a.key[f], a.nlevel[c], o, &sd);
-        const double ctr0 = o[0] + 0.5 * sd, ctr1 = o[1] + 0.5 * sd, ctr2 = o[2] + 0.5 * sd;
-        const double e0 = a.cx[c] - ctr0, e1 = a.cy[c] - ctr1, e2 = a.cz[c] - ctr2;
-        const double delta = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
-        const double bm = __longlong_as_double((long long)a.bmax[c]);
-        double rb;
-        if (P.mac == 1) rb = 0.5 * bm + sqrt(0.25 * bm * bm + sqrt(3.0 * a.B2[c] / P.a_err));
-        else rb = (P.theta > 0.0) ? sd / P.theta + delta : INFINITY;
-        const double hr = P.R2 + bm;   // Eq. (15) radius
-        const double sacc = fmax(rb, hr);
-        a.crit[c] = make_float2((float)(sacc * sacc), P.has_hard ? (float)(hr * hr) : -1.0f);
+        const SysParams &P = a.sp[s];
+        const SysBox &bx = a.box[s];
+        const uint32_t lev = a.nlevel[c];
+        uint32_t q[3];
+        prefix_q(a.key[f], lev, q);
+        const double sd = ldexp(bx.L, -(int)lev);
+        double rb, hr, delta;
+        if (F64) {
+            double o[3];
+            for (int k = 0; k < 3; ++k) o[k] = __dadd_rn(bx.lo[k], __dmul_rn((double)q[k], sd));
+            const double ctr0 = o[0] + 0.5 * sd, ctr1 = o[1] + 0.5 * sd, ctr2 = o[2] + 0.5 * sd;
+            const double e0 = a.cx[c] - ctr0, e1 = a.cy[c] - ctr1, e2 = a.cz[c] - ctr2;
+            delta = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+            const double bm = __longlong_as_double((long long)a.bmax[c]);
+            if (P.mac == 1) rb = 0.5 * bm + sqrt(0.25 * bm * bm + sqrt(3.0 * a.B2[c] / P.a_err));
+            else rb = (P.theta > 0.0) ? sd / P.theta + delta : INFINITY;
+            hr = P.R2 + bm;   // Eq. (15) radius
+            const double sacc = fmax(rb, hr);
+            a.crit[c] = make_float2((float)(sacc * sacc), P.has_hard ? (float)(hr * hr) : -1.0f);
+            a.nD[c] = make_double4_32a(a.cx[c], a.cy[c], a.cz[c], a.M[c]);
+            for (int k = 0; k < 3; ++k) a.org[3 * (size_t)c + k] = o[k];
+        } else {
+            const float sdf = ldexpf((float)bx.L, -(int)lev);
+            const float4 A = a.nA[c], B = a.nB[c];
+            // cell centre relative to the root corner: (q + 1/2) side, exact in FP32
+            const float e0 = (A.x - ((float)q[0] + 0.5f) * sdf) + B.x;
+            const float e1 = (A.y - ((float)q[1] + 0.5f) * sdf) + B.y;
+            const float e2 = (A.z - ((float)q[2] + 0.5f) * sdf) + B.z;
+            const float df = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+            const float bm = __uint_as_float(a.bmax32[c]);
+            float rbf;
+            if (P.mac == 1) rbf = 0.5f * bm + sqrtf(0.25f * bm * bm + sqrtf(3.0f * B.w / (float)P.a_err));
+            else rbf = (P.theta > 0.0) ? sdf / (float)P.theta + df : INFINITY;
+            const float hrf = P.R2f + bm;
+            const float sacc = fmaxf(rbf, hrf);
+            a.crit[c] = make_float2(sacc * sacc, P.has_hard ? hrf * hrf : -1.0f);
+            // FP64 copies (all lanes busy): moments, b_max, geometry
+            const double c0 = bx.lo[0] + ((double)A.x + (double)B.x), c1 = bx.lo[1] + ((double)A.y + (double)B.y),
+                         c2 = bx.lo[2] + ((double)A.z + (double)B.z);
+            a.M[c] = (double)A.w;
+            a.cx[c] = c0;
+            a.cy[c] = c1;
+            a.cz[c] = c2;
+            a.B2[c] = (double)B.w;
+            a.bmax[c] = (unsigned long long)__double_as_longlong((double)bm);
+            a.nD[c] = make_double4_32a(c0, c1, c2, (double)A.w);
+            for (int k = 0; k < 3; ++k) a.org[3 * (size_t)c + k] = __dadd_rn(bx.lo[k], __dmul_rn((double)q[k], sd));
+            rb = rbf;
+            hr = hrf;
+            delta = df;
+        }
         const uint32_t k = a.nnch[c];
         a.topo[c] = make_uint4(k ? a.nchild[c] : NONE, k, f, a.ncount[c]);
-        a.nD[c] = make_double4_32a(a.cx[c], a.cy[c], a.cz[c], a.M[c]);
         a.rb[c] = rb;
         a.hr[c] = hr;
         a.delta[c] = delta;
         a.side[c] = sd;
-        a.org[3 * (size_t)c + 0] = o[0];
-        a.org[3 * (size_t)c + 1] = o[1];
-        a.org[3 * (size_t)c + 2] = o[2];
     }
 }
 
@@ -1121,7 +1245,8 @@ void launch_moments(hybrid_ctx *c)
 {
     Status *st = status_dev(c);
     const int grid = grid_for(c, c->capNodes, 256, 8);
-    cudaMemsetAsync(c->nbmax.p, 0, (size_t)c->capNodes * sizeof(unsigned long long), c->st);
+    if (c->p.precision == 0) cudaMemsetAsync(c->nbmax.p, 0, (size_t)c->capNodes * sizeof(unsigned long long), c->st);
+    else cudaMemsetAsync(c->nbmax32.p, 0, (size_t)c->capNodes * sizeof(unsigned int), c->st);
     MomArgs a;
     a.lvl = (const uint32_t *)c->lvl.p;
     a.nfirst = (const uint32_t *)c->nfirst.p;
@@ -1162,18 +1287,21 @@ void launch_moments(hybrid_ctx *c)
         k_mom_chunks<false><<<gridw, 256, 0, c->st>>>(a, nitems, (const uint32_t *)c->nbig.p,
                                                       (const uint32_t *)c->mitems.p, (MomSums *)c->mpart.p, st);
     }
-    k_mom_big<<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
+    if (c->p.precision == 0)
+        k_mom_big<true><<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
+    else
+        k_mom_big<false><<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
     c->launches += 2;
     const int gridp = grid_for(c, c->N, 256, 8);
     if (c->p.precision == 0)
         k_bmax<true><<<gridp, 256, 0, c->st>>>(
             c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, a.x, a.y,
-            a.z, a.cx, a.cy, a.cz, nullptr, nullptr, nullptr, nullptr, (unsigned long long *)c->nbmax.p, st);
+            a.z, a.cx, a.cy, a.cz, nullptr, nullptr, nullptr, nullptr, (unsigned long long *)c->nbmax.p, nullptr, st);
     else
         k_bmax<false><<<gridp, 256, 0, c->st>>>(
             c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, nullptr,
             nullptr, nullptr, nullptr, nullptr, nullptr, (const float4 *)c->phi.p, (const float4 *)c->plo.p, a.nA, a.nB,
-            (unsigned long long *)c->nbmax.p, st);
+            nullptr, (unsigned int *)c->nbmax32.p, st);
     FinArgs f;
     f.lvl = a.lvl;
     f.nfirst = a.nfirst;
@@ -1185,12 +1313,15 @@ void launch_moments(hybrid_ctx *c)
     f.psys = a.psys;
     f.box = a.box;
     f.sp = (const SysParams *)c->sp_dev.p;
-    f.M = a.M;
-    f.cx = a.cx;
-    f.cy = a.cy;
-    f.cz = a.cz;
-    f.B2 = a.B2;
-    f.bmax = (const unsigned long long *)c->nbmax.p;
+    f.M = (double *)c->nM.p;
+    f.cx = (double *)c->ncx.p;
+    f.cy = (double *)c->ncy.p;
+    f.cz = (double *)c->ncz.p;
+    f.B2 = (double *)c->nB2.p;
+    f.bmax = (unsigned long long *)c->nbmax.p;
+    f.bmax32 = (const unsigned int *)c->nbmax32.p;
+    f.nA = (const float4 *)c->nA.p;
+    f.nB = (const float4 *)c->nB.p;
     f.crit = (float2 *)c->ncrit.p;
     f.topo = (uint4 *)c->ntopo.p;
     f.nD = (double4_32a *)c->nD.p;
@@ -1199,7 +1330,8 @@ void launch_moments(hybrid_ctx *c)
     f.delta = (double *)c->ndelta.p;
     f.side = (double *)c->nside.p;
     f.org = (double *)c->norg.p;
-    k_finalize<<<grid, 256, 0, c->st>>>(f, st);
+    if (c->p.precision == 0) k_finalize<true><<<grid, 256, 0, c->st>>>(f, st);
+    else k_finalize<false><<<grid, 256, 0, c->st>>>(f, st);
     c->launches += 3;
 }
 
