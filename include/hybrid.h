@@ -37,7 +37,8 @@ typedef enum {
     HYBRID_ENOMEM = 2,     /* device allocation failed */
     HYBRID_ECUDA = 3,      /* a CUDA runtime call failed */
     HYBRID_ECAPACITY = 4,  /* an internal buffer overflowed and could not be regrown */
-    HYBRID_ETIMEOUT = 5    /* a bounded device-side wait gave up */
+    HYBRID_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    HYBRID_ETOOLARGE = 6   /* input larger than a fixed-size scratch buffer holds */
 } hybrid_status;
 
 /* Method parameters (Sec. II; Sec. IV-A gives the paper's values).
@@ -195,6 +196,43 @@ int64_t hybrid_launch_count(hybrid_ctx *ctx);
  * summation on the device: kinetic and potential, returned to the host
  * (synchronises). Uses the context's eps and G (or sys->params). */
 hybrid_status hybrid_energy(hybrid_ctx *ctx, hybrid_system *sys, double *kinetic, double *potential);
+
+/* ---- allocation-free entry point ----
+ *
+ * The paper has no counterpart to this call: it is an interface addition for
+ * callers that cannot allocate device memory (no cudaMalloc/cudaFree or any
+ * allocating library call, torch's included) -- code that runs when the
+ * device has no free memory left (an out-of-memory handler, a process whose
+ * caching allocator holds the whole device) or a latency-sensitive loop that
+ * must not pay the implicit device synchronisation of cudaFree. Every other
+ * call here allocates through its context, so they cannot use those.
+ *
+ * hybrid_energy_noalloc computes what hybrid_energy does -- softened kinetic
+ * and potential energy by direct FP64 summation (Sec. IV-A total energy,
+ * potential of Eq. 2 with eps) -- for one system of n particles given as
+ * caller-owned DEVICE arrays (FP64, length n, any order), with G and eps
+ * passed directly and no context. Results are written to the two HOST
+ * doubles; the call enqueues two kernels and one 16-byte device-to-host copy
+ * on `stream` (a cudaStream_t; NULL = legacy default stream) and synchronises
+ * that stream before returning.
+ *
+ * Scratch is a fixed device array inside the library, sized for
+ * n <= HYBRID_ENERGY_NOALLOC_MAX_N (256 KB of FP64 partial sums); larger n returns
+ * HYBRID_ETOOLARGE before anything is enqueued. Its address is looked up once
+ * per device, on the first call made with that device current: make a first
+ * call (n = 0 is enough: it only does this set-up and returns zeros) before
+ * any stream capture. The scratch is shared by all calls on a device, so
+ * calls that overlap in time (two streams or two host threads) race on it and
+ * must be serialised by the caller. Nothing in the scratch has to start at
+ * zero: each call writes every slot it reads.
+ *
+ * Errors: HYBRID_EINVAL (n < 0, eps < 0, a NULL array with n > 0 or a NULL
+ * result pointer), HYBRID_ETOOLARGE, HYBRID_ECUDA (a failed launch, copy or
+ * look-up). */
+#define HYBRID_ENERGY_NOALLOC_MAX_N 4194304
+hybrid_status hybrid_energy_noalloc(int64_t n, const double *x, const double *y, const double *z, const double *vx,
+                                    const double *vy, const double *vz, const double *m, double G, double eps,
+                                    void *stream, double *kinetic, double *potential);
 
 #ifdef __cplusplus
 }

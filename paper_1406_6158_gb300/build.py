@@ -25,9 +25,10 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-
 FLAGS = {
     "tree.cu": ["--fmad=false"],
     "integrate.cu": ["--fmad=false"],
+    "energy_static.cu": ["--fmad=false"],
     "pair.cu": ["-ftz=true", "-prec-sqrt=false", "-prec-div=false"],
 }
-SOURCES = ["hybrid_api.cu", "scan.cu", "tree.cu", "walk.cu", "pair.cu", "integrate.cu"]
+SOURCES = ["hybrid_api.cu", "scan.cu", "tree.cu", "walk.cu", "pair.cu", "integrate.cu", "energy_static.cu"]
 
 
 def nvcc() -> str:

@@ -16,16 +16,18 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libhybrid.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT = range(6)
+OK, EINVAL, ENOMEM, ECUDA, ECAPACITY, ETIMEOUT, ETOOLARGE = range(7)
 STATUS_NAMES = {0: "HYBRID_OK", 1: "HYBRID_EINVAL", 2: "HYBRID_ENOMEM", 3: "HYBRID_ECUDA",
-                4: "HYBRID_ECAPACITY", 5: "HYBRID_ETIMEOUT"}
+                4: "HYBRID_ECAPACITY", 5: "HYBRID_ETIMEOUT", 6: "HYBRID_ETOOLARGE"}
+# largest n hybrid_energy_noalloc accepts (its fixed scratch size)
+ENERGY_NOALLOC_MAX_N = 4194304
 
 # every entry point declared in include/hybrid.h
 EXPORTS = (
     "hybrid_create", "hybrid_destroy", "hybrid_build_tree", "hybrid_soft_force", "hybrid_hard_force",
     "hybrid_kick", "hybrid_drift", "hybrid_step", "hybrid_step_batched", "hybrid_get_perm", "hybrid_sync",
     "hybrid_last_error", "hybrid_tree_info", "hybrid_tree_copy", "hybrid_lists_copy", "hybrid_interactions",
-    "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy",
+    "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy", "hybrid_energy_noalloc",
 )
 
 
@@ -90,6 +92,7 @@ def load() -> C.CDLL:
         "hybrid_profile": [ctx, C.c_int],
         "hybrid_profile_read": [ctx, C.c_int, P(D), P(I64), C.c_int],
         "hybrid_energy": [ctx, sysp, P(D), P(D)],
+        "hybrid_energy_noalloc": [I64, VP, VP, VP, VP, VP, VP, VP, D, D, VP, P(D), P(D)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -169,6 +172,26 @@ class System:
     def acc(self, which: str):
         import torch
         return torch.stack([self.t["a%s_%s" % (d, which)] for d in "xyz"], dim=1)
+
+
+def hybrid_energy_noalloc(x, y, z, vx, vy, vz, m, G: float, eps: float, stream=None):
+    """Kinetic and potential energy of one system through the allocation-free
+    entry point. Arrays are contiguous FP64 device tensors of one length;
+    `stream` is a torch.cuda.Stream or None (legacy default stream). Raises
+    HybridError on a non-OK status (ETOOLARGE above ENERGY_NOALLOC_MAX_N)."""
+    L = load()
+    n = int(x.numel())
+    for t in (x, y, z, vx, vy, vz, m):
+        if t.numel() != n or not t.is_contiguous():
+            raise ValueError("arrays must be contiguous and of one length")
+    T, W = C.c_double(), C.c_double()
+    st = None if stream is None else stream.cuda_stream
+    code = L.hybrid_energy_noalloc(n, *[_ptr(t) for t in (x, y, z, vx, vy, vz, m)], float(G), float(eps), st,
+                                   C.byref(T), C.byref(W))
+    if code != OK:
+        msg = ("n = %d exceeds the fixed scratch limit %d" % (n, ENERGY_NOALLOC_MAX_N)) if code == ETOOLARGE else ""
+        raise HybridError("hybrid_energy_noalloc", code, msg)
+    return T.value, W.value
 
 
 class Context:
