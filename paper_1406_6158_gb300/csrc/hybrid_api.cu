@@ -204,8 +204,8 @@ bool reserve(hybrid_ctx *c)
         ok = ok && ensure(c, c->list, (size_t)std::max<int64_t>(1 << 20, 128 * N) * 4);
         if (ok) c->capList = std::max<int64_t>(1 << 20, 128 * N);
     }
-    // pair work items: at most one per group plus one per 256 list entries
-    ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 4);
+    // pair work items (40 B each): at most one per group plus one per 256 list entries
+    ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 40);
     if (c->capStack == 0) c->capStack = 4096;
     ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * c->capStack * 4);
     // scratch of the scans: the longest scan is over max(N, nodes, 3 groups + 1, tiles x 256)
@@ -549,7 +549,7 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
             const int64_t cap = s.need[1] + s.need[1] / 4 + 1024;
             ok = ok && ensure(c, c->list, (size_t)cap * 4);
             if (ok) c->capList = cap;
-            ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 4);
+            ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 40);
         }
         if (s.need[2] > c->capStack) {
             ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * s.need[2] * 4);

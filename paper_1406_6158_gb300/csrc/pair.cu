@@ -31,6 +31,8 @@ constexpr int PAIR_WARPS = PAIR_THREADS / 32;
 constexpr int TILE = 64;
 constexpr int LCH_FAR = 512, LCH_NEAR = 256;
 
+struct WorkItem;
+
 struct PairArgs {
     const int64_t *ngroups;
     const uint32_t *gfirst, *gcount, *gsys;
@@ -44,8 +46,7 @@ struct PairArgs {
     unsigned long long *inter_soft, *inter_hard;   // pairs of the far kernel / of the near kernel
     const Status *st;
     // work items: chunks of at most lch list entries of one group
-    const uint32_t *wstart;   // [ng + 1]
-    const uint32_t *wmap;     // work item -> group
+    const WorkItem *items;
     const uint64_t *nwork;
     int lch;
     int want_soft, want_hard;
@@ -97,24 +98,24 @@ __device__ __forceinline__ float dll_K_precise(float r2u, float hx, float hy, fl
     return (Y2 * Y2 * Y2) * fmaf(Y2, fmaf(6.0f, Y2, -15.0f), 10.0f);
 }
 
-// near particle: soft += F (1 - K), hard += F K
+// near particle: soft += F (1 - K), hard += F K. (dx, dy, dz) = source - sink
+// and r2u = |.|^2 are computed by the caller; hh/ll are the source's raw hi
+// and lo parts and (shx, ..), (slx, ..) the sink's: hi differences are exact.
 template <bool SOFT, bool HARD>
-__device__ __forceinline__ void body_near(const float4 t, const float4 th, const float4 tl, float sx, float sy,
-                                          float sz, float shx, float shy, float shz, float slx, float sly, float slz,
-                                          const HardC &H, float &sax, float &say, float &saz, float &hax, float &hay,
-                                          float &haz)
+__device__ __forceinline__ void near_finish(float w, float dx, float dy, float dz, float r2u, const float4 &hh,
+                                            const float4 &ll, float shx, float shy, float shz, float slx, float sly,
+                                            float slz, const HardC &H, float &sax, float &say, float &saz, float &hax,
+                                            float &hay, float &haz)
 {
-    const float dx = t.x - sx, dy = t.y - sy, dz = t.z - sz;
-    const float r2u = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool inside = r2u < H.R2sq;
     if (!SOFT && !inside) return;
     const float r2 = r2u + H.eps2;
     const float ri = r2 > 0.0f ? rsqrtf(r2) : 0.0f;
-    const float f = t.w * ri * (ri * ri);
+    const float f = w * ri * (ri * ri);
     float K = 0.0f;
     if (inside)
-        K = dll_K_precise(r2u, __fsub_rn(th.x, shx), __fsub_rn(th.y, shy), __fsub_rn(th.z, shz),
-                          __fsub_rn(tl.x, slx), __fsub_rn(tl.y, sly), __fsub_rn(tl.z, slz), H);
+        K = dll_K_precise(r2u, __fsub_rn(hh.x, shx), __fsub_rn(hh.y, shy), __fsub_rn(hh.z, shz),
+                          __fsub_rn(ll.x, slx), __fsub_rn(ll.y, sly), __fsub_rn(ll.z, slz), H);
     if (SOFT) {
         const float fs = f * (1.0f - K);
         sax = fmaf(dx, fs, sax);
@@ -147,92 +148,121 @@ __device__ __forceinline__ int64_t next_item(unsigned long long *counter, int la
 }
 
 // ---------------------------------------------------------------------------
-// FP32 staging
+// FP32 work items and source staging
 // ---------------------------------------------------------------------------
-struct SrcCell {
-    __device__ __forceinline__ static void load(const PairArgs &a, uint32_t idx, float crx, float cry, float crz,
-                                                float4 &t, float4 &th, float4 &tl)
-    {
-        const float4 A = a.nA[idx], B = a.nB[idx];
-        t = make_float4((A.x - crx) + B.x, (A.y - cry) + B.y, (A.z - crz) + B.z, A.w);
-        th = tl = t;
-    }
+// A work item is the entry range [e0, e1) of one group's list, that list being
+// the group's cell run (entries e < Lc, at list[cbase + e]) followed by its
+// particle run (entries e >= Lc, at list[pbase + e] with pbase = start of the
+// particle run - Lc, modulo 2^64). The near lists have no cell run (Lc = 0).
+struct WorkItem {
+    uint64_t cbase, pbase;
+    uint32_t Lc, e0, e1, first;
+    uint32_t n;     // group size; bit 31 set when the group has several work items
+    uint32_t sys;
 };
-struct SrcPart {
-    __device__ __forceinline__ static void load(const PairArgs &a, uint32_t idx, float crx, float cry, float crz,
-                                                float4 &t, float4 &th, float4 &tl)
+static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
+constexpr uint32_t MULTI = 0x80000000u;
+
+// Raw sources (hi, lo float4 pairs of cells or particles) are gathered into a
+// ring of NST shared-memory stages with 16-byte cp.async copies issued
+// NST - 1 tiles ahead, from list indices loaded one tile before that; only
+// the rebasing to the group's reference point (one pass per staged entry,
+// by the lane that copied it) stands between a landed stage and its use.
+constexpr int NST = 3;
+constexpr int PER = TILE / 32;
+
+// Rebased sources: the near kernel keeps {x, y, z, m} in tile[0, TILE); the
+// far kernel keeps each source twice over, {x, x, y, y} {z, z, m, m}, for the
+// packed two-sink arithmetic, in tile[0, 2 PADT): entries from nt up to
+// PADT = TILE + 32 are zero-mass sources.
+constexpr int PADT = TILE + 32;
+struct WarpStage {
+    float4 tile[2 * PADT];
+    float4 rh[NST][TILE];     // raw hi parts (cells: nA, particles: phi)
+    float4 rl[NST][TILE];     // raw lo parts (cells: nB, particles: plo)
+};
+
+__device__ __forceinline__ void cp16(void *dst, const void *src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+struct ItemSrc {
+    uint64_t cbase, pbase;
+    uint32_t Lc, e0, e1;
+
+    __device__ __forceinline__ void load_idx(const PairArgs &a, int t, int lane, uint32_t (&idx)[PER]) const
     {
-        const float4 h = a.phi[idx], l = a.plo[idx];
-        const float hx = h.x - crx, hy = h.y - cry, hz = h.z - crz;
-        t = make_float4(hx + l.x, hy + l.y, hz + l.z, h.w);
-        th = make_float4(hx, hy, hz, 0.0f);
-        tl = l;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const uint32_t e = e0 + (uint32_t)(t * TILE + u * 32 + lane);
+            idx[u] = e < e1 ? a.list[(e < Lc ? cbase : pbase) + e] : 0u;
+        }
+    }
+    // gathers of tile t into stage t % NST; always closes one cp.async group
+    __device__ __forceinline__ void issue(const PairArgs &a, WarpStage &S, int t, int lane,
+                                          const uint32_t (&idx)[PER]) const
+    {
+        const int st = t % NST;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const uint32_t e = e0 + (uint32_t)(t * TILE + u * 32 + lane);
+            if (e < e1) {
+                const bool cell = e < Lc;
+                cp16(&S.rh[st][u * 32 + lane], (cell ? a.nA : a.phi) + idx[u]);
+                cp16(&S.rl[st][u * 32 + lane], (cell ? a.nB : a.plo) + idx[u]);
+            }
+        }
+        cp_commit();
     }
 };
 
-// One list range [q0, q1) against the lane's KS sinks.
-// MODE 0: far (weight 1, no guard), 1: far with the r = 0 guard, 2: near.
-template <int KS, int MODE, bool SOFT, bool HARD, typename SRC>
-__device__ __forceinline__ void sweep(const PairArgs &a, uint64_t q0, uint64_t q1, float4 *tile, float4 *tile_h,
-                                      float4 *tile_l, int lane, int copy, int copies, bool active, float crx, float cry,
-                                      float crz, const float (&sx)[KS], const float (&sy)[KS], const float (&sz)[KS],
-                                      const float (&shx)[KS], const float (&shy)[KS], const float (&shz)[KS],
-                                      const float (&slx)[KS], const float (&sly)[KS], const float (&slz)[KS],
-                                      const HardC &H, float (&ax)[KS], float (&ay)[KS], float (&az)[KS],
-                                      float (&bx)[KS], float (&by)[KS], float (&bz)[KS])
+// Runs the staging pipeline over the item's entries and calls
+// body(stage, nt) once per tile, after the tile has been rebased into S.tile.
+template <bool PACKED, typename Body>
+__device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, WarpStage &S, int lane, float crx,
+                                         float cry, float crz, Body &&body)
 {
-    constexpr int PER = TILE / 32;
-    constexpr bool NEAR = (MODE == 2);
-    float4 rt[PER], rh[PER], rl[PER];
-    auto fetch = [&](uint64_t t0) {
+    static_assert(NST == 3, "the prologue below is written for three stages");
+    const uint32_t ne = src.e1 - src.e0;
+    const int ntile = (int)((ne + TILE - 1) / TILE);
+    if (ntile == 0) return;
+    uint32_t i0[PER], i1[PER];
+    src.load_idx(a, 0, lane, i0);
+    src.load_idx(a, 1, lane, i1);
+    src.issue(a, S, 0, lane, i0);
+    src.issue(a, S, 1, lane, i1);
+    src.load_idx(a, 2, lane, i0);
+    for (int t = 0; t < ntile; ++t) {
+        src.issue(a, S, t + 2, lane, i0);   // no copies past the end, but one group per tile
+        if (t + 3 < ntile) src.load_idx(a, t + 3, lane, i0);
+        cp_wait<NST - 1>();                 // this lane's copies of tile t have landed
+        const int st = t % NST;
+        const int nt = (int)min((uint32_t)TILE, ne - (uint32_t)(t * TILE));
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const uint64_t e = t0 + (uint64_t)(u * 32 + lane);
-            if (e < q1) SRC::load(a, a.list[e], crx, cry, crz, rt[u], rh[u], rl[u]);
-        }
-    };
-    if (q0 < q1) fetch(q0);
-    for (uint64_t t0 = q0; t0 < q1; t0 += TILE) {
-        const int nt = (int)min((uint64_t)TILE, q1 - t0);
-#pragma unroll
-        for (int u = 0; u < PER; ++u) {
-            const int e = u * 32 + lane;
-            if (e < nt) {
-                tile[e] = rt[u];
-                if (NEAR) {
-                    tile_h[e] = rh[u];
-                    tile_l[e] = rl[u];
-                }
+        for (int u = 0; u < PER; ++u) {   // entries past nt become zero-mass sources
+            const int el = u * 32 + lane;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (el < nt) {
+                const float4 h = S.rh[st][el], l = S.rl[st][el];
+                v = make_float4((h.x - crx) + l.x, (h.y - cry) + l.y, (h.z - crz) + l.z, h.w);
+            }
+            if (PACKED) {
+                S.tile[2 * el] = make_float4(v.x, v.x, v.y, v.y);
+                S.tile[2 * el + 1] = make_float4(v.z, v.z, v.w, v.w);
+            } else {
+                S.tile[el] = v;
             }
         }
         __syncwarp();
-        if (t0 + TILE < q1) fetch(t0 + TILE);   // next tile's loads overlap this tile's arithmetic
-        if (active) {
-            int j = copy;
-            if (!NEAR) {   // two sources per round: one loop overhead per 2 KS interactions
-                for (; j + copies < nt; j += 2 * copies) {
-                    const float4 q0 = tile[j], q1 = tile[j + copies];
-#pragma unroll
-                    for (int k = 0; k < KS; ++k) {
-                        body_far<MODE == 1>(q0, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
-                        body_far<MODE == 1>(q1, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
-                    }
-                }
-            }
-            for (; j < nt; j += copies) {
-                const float4 q = tile[j];
-                if (!NEAR) {
-#pragma unroll
-                    for (int k = 0; k < KS; ++k) body_far<MODE == 1>(q, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
-                } else {
-                    const float4 qh = tile_h[j], ql = tile_l[j];
-#pragma unroll
-                    for (int k = 0; k < KS; ++k)
-                        body_near<SOFT, HARD>(q, qh, ql, sx[k], sy[k], sz[k], shx[k], shy[k], shz[k], slx[k], sly[k],
-                                              slz[k], H, ax[k], ay[k], az[k], bx[k], by[k], bz[k]);
-                }
-            }
-        }
+        body(st, nt);
         __syncwarp();
     }
 }
@@ -258,58 +288,114 @@ __device__ __forceinline__ void reduce_copies(int lane, int copy, int copies, in
     }
 }
 
+// ---- packed two-sink arithmetic (f32x2: one instruction, two FP32 lanes) ----
+__device__ __forceinline__ uint64_t pk2(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t v, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.ftz.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// the body of body_far for two sinks (S*) against one source given twice
+// over (X2 = {x, x}, ..): the same roundings per lane
+template <bool GUARD>
+__device__ __forceinline__ void body_far2(uint64_t X2, uint64_t Y2, uint64_t Z2, uint64_t M2, uint64_t SX, uint64_t SY,
+                                          uint64_t SZ, uint64_t E2, uint64_t &AX, uint64_t &AY, uint64_t &AZ)
+{
+    const uint64_t dx = sub2(X2, SX), dy = sub2(Y2, SY), dz = sub2(Z2, SZ);
+    const uint64_t r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, E2)));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    float ia = rsqrtf(ra), ib = rsqrtf(rb);
+    if (GUARD) {
+        ia = ra > 0.0f ? ia : 0.0f;
+        ib = rb > 0.0f ? ib : 0.0f;
+    }
+    const uint64_t ri = pk2(ia, ib);
+    const uint64_t f = mul2(mul2(M2, ri), mul2(ri, ri));
+    AX = fma2(dx, f, AX);
+    AY = fma2(dy, f, AY);
+    AZ = fma2(dz, f, AZ);
+}
+
+// The far sweep of one tile: copy c takes sources c, c + copies, ... Every
+// lane runs the same number of rounds of two sources (entries from nt to
+// PADT are zero-mass sources), so the loop has no divergence; lanes outside
+// the copies compute sums that are never used. KP sink pairs per lane.
+template <int KP, bool GUARD>
+__device__ __forceinline__ void far_tile(const WarpStage &S, int nt, int copy, int copies, uint64_t E2,
+                                         const uint64_t (&SX)[KP], const uint64_t (&SY)[KP], const uint64_t (&SZ)[KP],
+                                         uint64_t (&AX)[KP], uint64_t (&AY)[KP], uint64_t (&AZ)[KP])
+{
+    const int rounds = (nt + 2 * copies - 1) / (2 * copies);
+    uint32_t q = (uint32_t)__cvta_generic_to_shared(S.tile) + 32u * (uint32_t)copy;
+    const uint32_t step = 32u * (uint32_t)copies;
+    for (int m = 0; m < rounds; ++m, q += 2 * step) {
+        uint64_t X0, Y0, Z0, M0, X1, Y1, Z1, M1;
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(X0), "=l"(Y0) : "r"(q));
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(Z0), "=l"(M0) : "r"(q + 16));
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(X1), "=l"(Y1) : "r"(q + step));
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(Z1), "=l"(M1) : "r"(q + step + 16));
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            body_far2<GUARD>(X0, Y0, Z0, M0, SX[k], SY[k], SZ[k], E2, AX[k], AY[k], AZ[k]);
+            body_far2<GUARD>(X1, Y1, Z1, M1, SX[k], SY[k], SZ[k], E2, AX[k], AY[k], AZ[k]);
+        }
+    }
+}
+
 // NEAR = false: cells + far particles -> soft. NEAR = true: near particles ->
 // soft (1 - K) and/or hard (K), by SOFT/HARD.
 template <int KS, bool NEAR, bool SOFT, bool HARD>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
 {
-    constexpr int HT = NEAR ? TILE : 1;
-    __shared__ float4 tiles[PAIR_WARPS][TILE];
-    __shared__ float4 tiles_h[PAIR_WARPS][HT];
-    __shared__ float4 tiles_l[PAIR_WARPS][HT];
+    __shared__ WarpStage stages[PAIR_WARPS];
     if (a.st->code) return;
     const int lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    float4 *tile = tiles[wid];
-    float4 *tile_h = tiles_h[wid];
-    float4 *tile_l = tiles_l[wid];
-    const int64_t ng = *a.ngroups;
+    WarpStage &S = stages[threadIdx.x >> 5];
+    for (int e = 2 * TILE + lane; e < 2 * PADT; e += 32) S.tile[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int64_t W = (int64_t)*a.nwork;
     unsigned long long inter = 0;
-    for (;;) {
-        const int64_t w = next_item(a.counter, lane);
-        if (w >= W) break;
-        const uint32_t g = a.wmap[w];
-        const uint32_t ws0 = a.wstart[g];
-        const int nchunk = (int)(a.wstart[g + 1] - ws0);
-        const uint64_t k = (uint64_t)(w - ws0);
-        const uint32_t first = a.gfirst[g];
-        const int n = (int)a.gcount[g];
-        const SysParams &P = a.sp[a.gsys[g]];
+    int64_t w = next_item(a.counter, lane);
+    while (w < W) {
+        const int64_t wn = next_item(a.counter, lane);   // the next item's number arrives while this one runs
+        const WorkItem d = a.items[w];
+        const SysParams &P = a.sp[d.sys];
         HardC H;
         H.eps2 = P.eps2f;
         H.R2 = P.R2f;
         H.R2sq = P.R2sqf;
         H.R2sqlo = P.R2sqlo;
         H.invdR = P.invdRf;
+        const ItemSrc src = {d.cbase, d.pbase, d.Lc, d.e0, d.e1};
+        const uint32_t first = d.first;
+        const int n = (int)(d.n & ~MULTI);
+        const bool multi = (d.n & MULTI) != 0;
         const float4 cref = a.phi[first];
         const float crx = cref.x, cry = cref.y, crz = cref.z;
-        uint64_t c0, c1, p0, p1;
-        if (!NEAR) {
-            c0 = a.off[g];
-            c1 = a.off[g + 1];
-            p0 = a.off[ng + g];
-            p1 = a.off[ng + g + 1];
-        } else {
-            c0 = c1 = 0;
-            p0 = a.off[2 * ng + g];
-            p1 = a.off[2 * ng + g + 1];
-        }
-        const uint64_t Lc = c1 - c0, L = Lc + (p1 - p0);
-        const uint64_t e0 = k * (uint64_t)a.lch, e1 = min(L, e0 + (uint64_t)a.lch);
-        const uint64_t qc0 = c0 + min(e0, Lc), qc1 = c0 + min(e1, Lc);
-        const uint64_t qp0 = p0 + (e0 > Lc ? e0 - Lc : 0), qp1 = p0 + (e1 > Lc ? e1 - Lc : 0);
-        inter += (unsigned long long)n * (e1 > e0 ? e1 - e0 : 0);
+        inter += (unsigned long long)n * (d.e1 - d.e0);
         const int lpc = n <= 32 * KS ? (n + KS - 1) / KS : 32;
         const int copies = 32 / lpc;
         const int copy = lane / lpc, slot = lane - copy * lpc;
@@ -323,34 +409,78 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                 int si = r0 + kk * lpc + slot;
                 si = si < n ? si : n - 1;
                 const float4 h = a.phi[first + si], l = a.plo[first + si];
-                shx[kk] = h.x - crx;
-                shy[kk] = h.y - cry;
-                shz[kk] = h.z - crz;
+                shx[kk] = h.x;
+                shy[kk] = h.y;
+                shz[kk] = h.z;
                 slx[kk] = l.x;
                 sly[kk] = l.y;
                 slz[kk] = l.z;
-                sx[kk] = shx[kk] + l.x;
-                sy[kk] = shy[kk] + l.y;
-                sz[kk] = shz[kk] + l.z;
+                sx[kk] = (h.x - crx) + l.x;
+                sy[kk] = (h.y - cry) + l.y;
+                sz[kk] = (h.z - crz) + l.z;
                 ax[kk] = ay[kk] = az[kk] = 0.0f;
                 bx[kk] = by[kk] = bz[kk] = 0.0f;
             }
             if (!NEAR) {
-                sweep<KS, 0, true, false, SrcCell>(a, qc0, qc1, tile, tile_h, tile_l, lane, copy, copies, active, crx,
-                                                    cry, crz, sx, sy, sz, shx, shy, shz, slx, sly, slz, H, ax, ay, az,
-                                                    bx, by, bz);
+                constexpr int KP = (KS + 1) / 2;
+                uint64_t SX[KP], SY[KP], SZ[KP], AX[KP], AY[KP], AZ[KP];
+#pragma unroll
+                for (int p = 0; p < KP; ++p) {
+                    const int k1 = 2 * p + 1 < KS ? 2 * p + 1 : 2 * p;
+                    SX[p] = pk2(sx[2 * p], sx[k1]);
+                    SY[p] = pk2(sy[2 * p], sy[k1]);
+                    SZ[p] = pk2(sz[2 * p], sz[k1]);
+                    AX[p] = AY[p] = AZ[p] = 0ull;
+                }
+                const uint64_t E2 = pk2(H.eps2, H.eps2);
                 if (H.eps2 > 0.0f)
-                    sweep<KS, 0, true, false, SrcPart>(a, qp0, qp1, tile, tile_h, tile_l, lane, copy, copies, active,
-                                                        crx, cry, crz, sx, sy, sz, shx, shy, shz, slx, sly, slz, H, ax,
-                                                        ay, az, bx, by, bz);
-                else
-                    sweep<KS, 1, true, false, SrcPart>(a, qp0, qp1, tile, tile_h, tile_l, lane, copy, copies, active,
-                                                        crx, cry, crz, sx, sy, sz, shx, shy, shz, slx, sly, slz, H, ax,
-                                                        ay, az, bx, by, bz);
+                    pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
+                        far_tile<KP, false>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                    });
+                else   // eps = 0 without a hard part: a sink meets itself in its far particles
+                    pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
+                        far_tile<KP, true>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                    });
+#pragma unroll
+                for (int p = 0; p < KP; ++p) {
+                    float t0, t1;
+                    upk2(AX[p], t0, t1);
+                    ax[2 * p] = t0;
+                    if (2 * p + 1 < KS) ax[2 * p + 1] = t1;
+                    upk2(AY[p], t0, t1);
+                    ay[2 * p] = t0;
+                    if (2 * p + 1 < KS) ay[2 * p + 1] = t1;
+                    upk2(AZ[p], t0, t1);
+                    az[2 * p] = t0;
+                    if (2 * p + 1 < KS) az[2 * p + 1] = t1;
+                }
             } else {
-                sweep<KS, 2, SOFT, HARD, SrcPart>(a, qp0, qp1, tile, tile_h, tile_l, lane, copy, copies, active, crx,
-                                                   cry, crz, sx, sy, sz, shx, shy, shz, slx, sly, slz, H, ax, ay, az, bx,
-                                                   by, bz);
+                pipeline<false>(a, src, S, lane, crx, cry, crz, [&](int st, int nt) {
+                    if (!active) return;
+                    for (int j = copy; j < nt; j += copies) {
+                        const float4 q = S.tile[j];
+                        float dx[KS], dy[KS], dz[KS], r2u[KS];
+                        bool any_in = false;
+#pragma unroll
+                        for (int k = 0; k < KS; ++k) {
+                            dx[k] = q.x - sx[k];
+                            dy[k] = q.y - sy[k];
+                            dz[k] = q.z - sz[k];
+                            r2u[k] = fmaf(dx[k], dx[k], fmaf(dy[k], dy[k], dz[k] * dz[k]));
+                            any_in |= r2u[k] < H.R2sq;
+                        }
+                        float4 hh = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ll = hh;
+                        if (any_in) {
+                            hh = S.rh[st][j];
+                            ll = S.rl[st][j];
+                        }
+#pragma unroll
+                        for (int k = 0; k < KS; ++k)
+                            near_finish<SOFT, HARD>(q.w, dx[k], dy[k], dz[k], r2u[k], hh, ll, shx[k], shy[k], shz[k],
+                                                    slx[k], sly[k], slz[k], H, ax[k], ay[k], az[k], bx[k], by[k],
+                                                    bz[k]);
+                    }
+                });
             }
             if (SOFT) reduce_copies<KS>(lane, copy, copies, lpc, ax, ay, az);
             if (HARD) reduce_copies<KS>(lane, copy, copies, lpc, bx, by, bz);
@@ -363,11 +493,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                         const uint32_t i = first + si;
                         if (SOFT) {
                             float *ox = (float *)a.as[0], *oy = (float *)a.as[1], *oz = (float *)a.as[2];
-                            if (!NEAR && nchunk == 1) {
+                            if (!NEAR && !multi) {
                                 ox[i] = Gf * ax[kk];
                                 oy[i] = Gf * ay[kk];
                                 oz[i] = Gf * az[kk];
-                            } else {   // several chunks, or the near part added to the far part
+                            } else {   // several items, or the near part added to the far part
                                 atomicAdd(ox + i, Gf * ax[kk]);
                                 atomicAdd(oy + i, Gf * ay[kk]);
                                 atomicAdd(oz + i, Gf * az[kk]);
@@ -375,7 +505,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                         }
                         if (HARD) {
                             float *ox = (float *)a.ah[0], *oy = (float *)a.ah[1], *oz = (float *)a.ah[2];
-                            if (nchunk == 1) {
+                            if (!multi) {
                                 ox[i] = Gf * bx[kk];
                                 oy[i] = Gf * by[kk];
                                 oz[i] = Gf * bz[kk];
@@ -389,13 +519,25 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                 }
             }
         }
+        w = wn;
     }
+    cp_wait<0>();   // nothing may stay in flight into shared memory at exit
     if (lane == 0) atomicAdd(NEAR ? a.inter_hard : a.inter_soft, inter);
 }
 
-// work items per group: max(1, ceil(list length / lch))
+// Entries per work item of a group of n sinks: lch for n >= 64, longer runs
+// (up to 8 lch) for smaller groups, so that items cost about the same
+// n x entries and a small group pays the per-item set-up less often.
+__device__ __forceinline__ uint64_t item_len(uint32_t n, int lch)
+{
+    const uint32_t f = n >= 64 ? 1u : min(8u, 64u / max(n, 1u));
+    return (uint64_t)lch * f;
+}
+
+// work items per group: max(1, ceil(list length / item_len))
 __global__ void __launch_bounds__(256) k_pair_plan(const int64_t *__restrict__ ngroups,
-                                                   const uint64_t *__restrict__ off, int near, int lch,
+                                                   const uint64_t *__restrict__ off,
+                                                   const uint32_t *__restrict__ gcount, int near, int lch,
                                                    uint32_t *__restrict__ wcount, const Status *st)
 {
     if (st->code) return;
@@ -403,13 +545,18 @@ __global__ void __launch_bounds__(256) k_pair_plan(const int64_t *__restrict__ n
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t L = near ? (off[2 * ng + g + 1] - off[2 * ng + g])
                                 : (off[g + 1] - off[g]) + (off[ng + g + 1] - off[ng + g]);
-        wcount[g] = (uint32_t)max((uint64_t)1, (L + lch - 1) / (uint64_t)lch);
+        const uint64_t len = item_len(gcount[g], lch);
+        wcount[g] = (uint32_t)max((uint64_t)1, (L + len - 1) / len);
     }
 }
 
+// the work items of every group, from the scanned item counts
 __global__ void __launch_bounds__(256) k_pair_map(const int64_t *__restrict__ ngroups, uint32_t *__restrict__ wstart,
-                                                  const uint64_t *__restrict__ total, uint32_t *__restrict__ wmap,
-                                                  const Status *st)
+                                                  const uint64_t *__restrict__ total, const uint64_t *__restrict__ off,
+                                                  const uint32_t *__restrict__ gfirst,
+                                                  const uint32_t *__restrict__ gcount,
+                                                  const uint32_t *__restrict__ gsys, int near, int lch,
+                                                  WorkItem *__restrict__ items, const Status *st)
 {
     if (st->code) return;
     const int64_t ng = *ngroups;
@@ -417,8 +564,30 @@ __global__ void __launch_bounds__(256) k_pair_map(const int64_t *__restrict__ ng
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t s0 = wstart[g];
         const uint32_t s1 = (g + 1 < ng) ? wstart[g + 1] : T;
-        for (uint32_t w = s0; w < s1; ++w) wmap[w] = (uint32_t)g;
-        if (g == ng - 1) wstart[ng] = T;
+        uint64_t c0 = 0, Lc = 0, p0, L;
+        if (near) {
+            p0 = off[2 * ng + g];
+            L = off[2 * ng + g + 1] - p0;
+        } else {
+            c0 = off[g];
+            Lc = off[g + 1] - c0;
+            p0 = off[ng + g];
+            L = Lc + (off[ng + g + 1] - p0);
+        }
+        WorkItem d;
+        d.cbase = c0;
+        d.pbase = p0 - Lc;
+        d.Lc = (uint32_t)Lc;
+        d.first = gfirst[g];
+        d.n = gcount[g] | (s1 - s0 > 1 ? MULTI : 0u);
+        d.sys = gsys[g];
+        const uint64_t len = item_len(gcount[g], lch);
+        for (uint32_t w = s0; w < s1; ++w) {
+            const uint64_t e0 = (uint64_t)(w - s0) * len;
+            d.e0 = (uint32_t)e0;
+            d.e1 = (uint32_t)min(L, e0 + len);
+            items[w] = d;
+        }
     }
 }
 
@@ -540,8 +709,7 @@ void fill_args(hybrid_ctx *c, PairArgs &a)
     a.inter_soft = ctr + 6;
     a.inter_hard = ctr + 7;
     a.st = status_dev(c);
-    a.wstart = nullptr;
-    a.wmap = nullptr;
+    a.items = nullptr;
     a.nwork = nullptr;
     a.lch = 0;
     a.want_soft = a.want_hard = 0;
@@ -554,14 +722,14 @@ void go_f32(hybrid_ctx *c, const PairArgs &a)
 }
 
 // Sinks per lane KS = ceil(n_crit / threads_per_group), from 1 to 4; the
-// default is 4 for the far kernel (one shared-memory read feeds 4
-// interactions) and 2 for the near kernel (it also keeps hi/lo offsets per sink).
+// default is 4 (one shared-memory read feeds 4 interactions; the far kernel
+// runs them as two packed sink pairs).
 template <bool NEAR, bool SOFT, bool HARD>
 void go_ks(hybrid_ctx *c, const PairArgs &a)
 {
     int ks;
     if (c->p.threads_per_group > 0) ks = (c->p.n_crit + c->p.threads_per_group - 1) / c->p.threads_per_group;
-    else ks = NEAR ? (c->p.n_crit > 64 ? 4 : 2) : 4;
+    else ks = 4;
     ks = ks <= 1 ? 1 : (ks <= 2 ? 2 : 4);
     if (ks == 1) go_f32<1, NEAR, SOFT, HARD>(c, a);
     else if (ks == 2) go_f32<2, NEAR, SOFT, HARD>(c, a);
@@ -592,11 +760,11 @@ void launch_pairs(hybrid_ctx *c, bool near, int mode)
         uint32_t *wstart = (uint32_t *)c->wstart.p;
         uint64_t *d_total = (uint64_t *)c->counter.p + 8;
         const int gridg = (int)std::max<int64_t>(1, std::min<int64_t>((c->capGroups + 255) / 256, c->nsm * 8));
-        k_pair_plan<<<gridg, 256, 0, c->st>>>(a.ngroups, a.off, near ? 1 : 0, lch, wstart, st);
+        k_pair_plan<<<gridg, 256, 0, c->st>>>(a.ngroups, a.off, a.gcount, near ? 1 : 0, lch, wstart, st);
         scan_u32(c, wstart, 0, a.ngroups, c->capGroups, d_total);
-        k_pair_map<<<gridg, 256, 0, c->st>>>(a.ngroups, wstart, d_total, (uint32_t *)c->wmap.p, st);
-        a.wstart = wstart;
-        a.wmap = (const uint32_t *)c->wmap.p;
+        k_pair_map<<<gridg, 256, 0, c->st>>>(a.ngroups, wstart, d_total, a.off, a.gfirst, a.gcount, a.gsys,
+                                             near ? 1 : 0, lch, (WorkItem *)c->wmap.p, st);
+        a.items = (const WorkItem *)c->wmap.p;
         a.nwork = d_total;
         a.lch = lch;
         if (!near)
