@@ -195,10 +195,11 @@ bool reserve(hybrid_ctx *c)
         if (ok) c->capS = S;
     }
     if (c->nchunks > c->capChunks) {
-        ok = ok && ensure(c, c->chunks_dev, (size_t)c->nchunks * sizeof(Chunk)) &&
-             ensure(c, c->hist, (size_t)c->nchunks * 256 * 4);
+        ok = ok && ensure(c, c->chunks_dev, (size_t)c->nchunks * sizeof(Chunk));
         if (ok) c->capChunks = c->nchunks;
     }
+    // radix sort scratch: 64 tickets, digit counts [S][8][256], look-back words [8][chunks][256]
+    ok = ok && ensure(c, c->hist, ((size_t)64 + (size_t)2048 * (S + c->nchunks)) * 4);
     if (c->capNodes < std::max<int64_t>(4096, N)) ok = ok && alloc_nodes(c, std::max<int64_t>(4096, N));
     if (c->capList < std::max<int64_t>(1 << 20, 128 * N)) {
         ok = ok && ensure(c, c->list, (size_t)std::max<int64_t>(1 << 20, 128 * N) * 4);

@@ -167,64 +167,94 @@ __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restric
 }
 
 // ---------------------------------------------------------------------------
-// Stable LSD radix sort, 8-bit digits, tiles of RS_TILE keys inside one
-// system. The histogram of tile c for digit d goes to slot
-//   256 * first_chunk(s) + d * nchunk(s) + (c - first_chunk(s)),
-// so one flat exclusive scan yields, for every (tile, digit), the start of
-// its run inside its own system's segment.
+// Stable LSD radix sort, 8-bit digits, one launch per digit.
+// k_digit_counts counts, per system, the digits of all eight passes. Pass p
+// runs k_onesweep: tiles (chunks of at most ctx->tile keys inside one system)
+// are claimed in order from a ticket counter; a tile ranks its keys (stable:
+// warp-striped input order), publishes its per-digit counts, then adds up
+// the counts of the earlier tiles of its system by reading their published
+// words backwards until it meets an inclusive prefix (a chained scan with
+// look-back), and publishes its own inclusive prefix. A key's destination is
+// the system's start + the system's count of smaller digits + the earlier
+// tiles' count of its digit + its rank in the tile. Tiles only wait on tiles
+// with smaller tickets, which were claimed by running blocks and publish
+// their counts before they wait on anything; every wait is bounded.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t hist_slot(const Chunk &ch, int c, uint32_t d)
+constexpr uint32_t LB_AGG = 1u << 30, LB_INC = 2u << 30, LB_CNT = (1u << 30) - 1u;
+constexpr int LB_SPIN_MAX = 1 << 22;
+// sort scratch layout (u32): [0, 64) tickets, then counts[S][8][256], then look[8][nchunks][256]
+constexpr int RS_HDR = 64;
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p)
 {
-    return 256u * (uint32_t)ch.first_chunk + d * (uint32_t)ch.nchunk + (uint32_t)(c - ch.first_chunk);
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_radix_hist(const uint64_t *__restrict__ key, const Chunk *__restrict__ chunks,
-                                                    int nchunks, int shift, uint32_t *__restrict__ hist,
-                                                    const Status *st)
+__global__ void __launch_bounds__(256) k_digit_counts(const uint64_t *__restrict__ key, const Chunk *__restrict__ chunks,
+                                                      int nchunks, uint32_t *__restrict__ counts)
 {
-    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
-    __shared__ uint32_t h[256];
+    __shared__ uint32_t h[8][256];
     const int lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1u;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const Chunk ch = chunks[c];
-        h[threadIdx.x] = 0;
+        for (int t = threadIdx.x; t < 8 * 256; t += blockDim.x) (&h[0][0])[t] = 0;
         __syncthreads();
         for (int i0 = 0; i0 < ch.len; i0 += blockDim.x) {
             const int i = i0 + threadIdx.x;
             const bool ok = i < ch.len;
-            const uint32_t d = ok ? (uint32_t)(key[ch.start + i] >> shift) & 0xffu : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            if (ok && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[d], (uint32_t)__popc(peers));
+            const uint64_t k = ok ? key[ch.start + i] : 0ull;
+#pragma unroll
+            for (int p = 0; p < 8; ++p) {
+                const uint32_t d = ok ? (uint32_t)(k >> (8 * p)) & 0xffu : 256u;
+                const unsigned peers = __match_any_sync(0xffffffffu, d);
+                if (ok && (peers & ltmask) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+            }
         }
         __syncthreads();
-        hist[hist_slot(ch, c, threadIdx.x)] = h[threadIdx.x];
+        uint32_t *dst = counts + (size_t)ch.sys * 2048;
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+            const uint32_t v = (&h[0][0])[t];
+            if (v) atomicAdd(dst + t, v);
+        }
         __syncthreads();
     }
 }
 
 template <int IPT>
-__global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restrict__ kin,
-                                                       const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                                                       uint32_t *__restrict__ vout,
-                                                       const Chunk *__restrict__ chunks, int nchunks, int shift,
-                                                       const uint32_t *__restrict__ offs, const Status *st)
+__global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                  uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                  const Chunk *__restrict__ chunks, int nchunks, int pass,
+                                                  const uint32_t *__restrict__ counts, uint32_t *look,
+                                                  uint32_t *ticket, int64_t ntotal, Status *st)
 {
-    (void)st;   // the sort always runs: later kernels rely on a consistent permutation
+    // the sort always runs (later kernels rely on a consistent permutation); st only records a timeout
     __shared__ uint32_t whist[RS_WARPS][256];
     __shared__ uint32_t base[256];
+    __shared__ uint32_t wsum[RS_WARPS];
+    __shared__ int cid;
+    const int shift = 8 * pass;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned ltmask = (1u << lane) - 1u;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const Chunk ch = chunks[c];
+    for (;;) {
+        if (threadIdx.x == 0) cid = (int)atomicAdd(ticket, 1u);
         for (int t = threadIdx.x; t < RS_WARPS * 256; t += blockDim.x) (&whist[0][0])[t] = 0;
-        base[threadIdx.x] = offs[hist_slot(ch, c, threadIdx.x)];
         __syncthreads();
+        const int c = cid;
+        if (c >= nchunks) break;
+        const Chunk ch = chunks[c];
         uint64_t k[IPT];
         uint32_t v[IPT], r[IPT];
         const int wbase = w * 32 * IPT;
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
-            const int li = wbase + it * 32 + lane;     // warp-striped: (it, lane) is input order
+            const int li = wbase + it * 32 + lane;   // warp-striped: (it, lane) is input order
             const bool ok = li < ch.len;
             k[it] = ok ? kin[ch.start + li] : 0ull;
             v[it] = ok ? vin[ch.start + li] : 0u;
@@ -237,24 +267,61 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t *__restric
             r[it] = before + (uint32_t)__popc(peers & ltmask);
         }
         __syncthreads();
-        {   // exclusive prefix over the warps, per digit (warp order = input order)
-            const int d = threadIdx.x;
-            uint32_t run = 0;
-            for (int ww = 0; ww < RS_WARPS; ++ww) {
-                const uint32_t cnt = whist[ww][d];
-                whist[ww][d] = run;
-                run += cnt;
-            }
+        const int d = threadIdx.x;
+        uint32_t run = 0;   // tile count of digit d; whist becomes the exclusive prefix over the warps
+        for (int ww = 0; ww < RS_WARPS; ++ww) {
+            const uint32_t cnt = whist[ww][d];
+            whist[ww][d] = run;
+            run += cnt;
         }
+        uint32_t *mine = look + (size_t)c * 256 + d;
+        const bool first = (c == ch.first_chunk);
+        st_relaxed_u32(mine, (first ? LB_INC : LB_AGG) | run);
+        uint32_t excl = 0;
+        if (!first) {
+            for (int j = c - 1; j >= ch.first_chunk; --j) {
+                const uint32_t *q = look + (size_t)j * 256 + d;
+                uint32_t vq = ld_relaxed_u32(q);
+                int spins = 0;
+                while ((vq & (LB_AGG | LB_INC)) == 0u) {
+                    if (++spins > LB_SPIN_MAX) {
+                        fail(st, 5, -1);   // HYBRID_ETIMEOUT
+                        vq = LB_INC;
+                        break;
+                    }
+                    __nanosleep(64);
+                    vq = ld_relaxed_u32(q);
+                }
+                excl += vq & LB_CNT;
+                if (vq & LB_INC) break;
+            }
+            st_relaxed_u32(mine, LB_INC | (excl + run));
+        }
+        // exclusive prefix over digits of the system's counts (block scan, 256 threads)
+        const uint32_t cd = counts[(size_t)ch.sys * 2048 + pass * 256 + d];
+        uint32_t incl = cd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[w] = incl;
         __syncthreads();
+        uint32_t wpre = 0;
+        for (int ww = 0; ww < w; ++ww) wpre += wsum[ww];
+        base[d] = wpre + incl - cd + excl;
+        __syncthreads();
+        const int64_t s0 = chunks[ch.first_chunk].start;
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
             const int li = wbase + it * 32 + lane;
             if (li < ch.len) {
-                const uint32_t d = (uint32_t)(k[it] >> shift) & 0xffu;
-                const uint32_t dst = base[d] + whist[w][d] + r[it];
-                kout[dst] = k[it];
-                vout[dst] = v[it];
+                const uint32_t dd = (uint32_t)(k[it] >> shift) & 0xffu;
+                const int64_t dst = s0 + (int64_t)(base[dd] + whist[w][dd] + r[it]);
+                if (dst < ntotal) {   // always true unless a look-back timed out (recorded in st)
+                    kout[dst] = k[it];
+                    vout[dst] = v[it];
+                }
             }
         }
         __syncthreads();
@@ -1163,19 +1230,22 @@ void launch_keys_sort_permute(hybrid_ctx *c)
                                                     (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0,
                                                     st);
     c->launches++;
-    const int grid = std::min(c->nchunks, c->nsm * 8);
-    uint32_t *hist = (uint32_t *)c->hist.p;
+    uint32_t *rs = (uint32_t *)c->hist.p;
+    uint32_t *counts = rs + RS_HDR, *look = counts + (size_t)2048 * c->S;
+    cudaMemsetAsync(rs, 0, ((size_t)RS_HDR + (size_t)2048 * (c->S + c->nchunks)) * sizeof(uint32_t), c->st);
+    k_digit_counts<<<std::min(c->nchunks, c->nsm * 4), 256, 0, c->st>>>(k0, (const Chunk *)c->chunks_dev.p, c->nchunks,
+                                                                       counts);
+    c->launches++;
+    const int grid = std::min(c->nchunks, c->nsm * 4);
+    const Chunk *chk = (const Chunk *)c->chunks_dev.p;
     for (int pass = 0; pass < 8; ++pass) {
-        const int shift = 8 * pass;
-        k_radix_hist<<<grid, 256, 0, c->st>>>(k0, (const Chunk *)c->chunks_dev.p, c->nchunks, shift, hist, st);
-        c->launches++;
-        scan_u32(c, hist, (int64_t)c->nchunks * 256, nullptr, (int64_t)c->nchunks * 256, nullptr, true);
-        const Chunk *chk = (const Chunk *)c->chunks_dev.p;
+        uint32_t *lk = look + (size_t)pass * 256 * c->nchunks;
+        uint32_t *tk = rs + pass;
         switch (c->ipt) {
-        case 2: k_radix_scatter<2><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
-        case 4: k_radix_scatter<4><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
-        case 8: k_radix_scatter<8><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st); break;
-        default: k_radix_scatter<16><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, shift, hist, st);
+        case 2: k_onesweep<2><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
+        case 4: k_onesweep<4><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
+        case 8: k_onesweep<8><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
+        default: k_onesweep<16><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st);
         }
         c->launches++;
         std::swap(k0, k1);
