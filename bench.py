@@ -178,10 +178,108 @@ def run_reference(args, w):
     return 0
 
 
+def c4_systems(count=512, seed=3):
+    """The batched ensemble: `count` Plummer spheres, N log-uniform in [2^10, 2^17], eps = 1/(4 N^(1/3))."""
+    from paper_1406_6158_gb300 import ics
+    sizes = ics.ensemble_sizes(count, 10.0, 17.0, seed)
+    out = []
+    for k, n in enumerate(sizes):
+        eps = 1.0 / (4.0 * float(n) ** (1.0 / 3.0))
+        out.append((int(n), seed * 1000003 + k, dict(eps=eps, theta=0.5, R1=4 * eps, R2=8 * eps, dt_soft=1.0 / 128)))
+    return out
+
+
+def run_c4(args):
+    """Batched FP32 form (one call advances all systems; autotuned n_crit, threads per group, staging depth)
+    against the plain form (FP64, one system per call), same systems, one soft step each."""
+    import numpy as np
+    import torch
+    from paper_1406_6158_gb300 import build as cuda_build
+    from paper_1406_6158_gb300 import hybrid, ics
+    cuda_build.build()
+    specs = c4_systems(args.c4_count)
+    total = sum(n for n, _, _ in specs)
+    states = [ics.plummer(n, sd) for n, sd, _ in specs]
+    base = dict(n_hard=4, n_leaf=16, n_crit=64)
+
+    def per(prec, kw):
+        return hybrid.Params(precision=prec, **base, **kw)
+
+    stream = torch.cuda.current_stream()
+    # ---- batched FP32 ----
+    ctx = hybrid.Context(per(1, specs[0][2]), stream)
+    sysb = [hybrid.System(st, precision=1, ids=False, params=per(1, kw)) for st, (_, _, kw) in zip(states, specs)]
+    chosen, table = ctx.hybrid_autotune(sysb)
+    ctx.hybrid_step_batched(sysb, 0)
+    for _ in range(args.warmup):
+        ctx.hybrid_step_batched(sysb, 1)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clocks = ClockSampler(0)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = ctx.hybrid_launch_count()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.hybrid_step_batched(sysb, 1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.hybrid_launch_count() - launches0
+    t_b = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    v_b = total * args.steps / t_b
+    # ---- plain FP64, one system per call ----
+    ctx64 = hybrid.Context(per(0, specs[0][2]), stream)
+    sys64 = [hybrid.System(st, precision=0, ids=False, params=per(0, kw)) for st, (_, _, kw) in zip(states, specs)]
+    for s in sys64:
+        ctx64.hybrid_step(s, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in sys64:
+        ctx64.hybrid_step(s, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_p = e0.elapsed_time(e1) / 1e3
+    v_p = total / t_p
+    # ---- force error against direct summation on a few systems ----
+    rng = np.random.default_rng(7)
+    pick = sorted(rng.choice(len(specs), 4, replace=False))
+    errs = {"fp32_batched": [], "fp64_plain": []}
+    for k in pick:
+        for name, sysl in (("fp32_batched", sysb), ("fp64_plain", sys64)):
+            out = sysl[k].numpy()
+            a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+            a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+            errs[name].append(force_error_rms(out, a_s, a_h, specs[k][2]["eps"], nsample=256))
+    line = {
+        "metric": METRIC, "value": v_b, "unit": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched ensemble: %d Plummer spheres, N log-uniform in [2^10, 2^17] (seed 3), "
+                               "total N=%d, eps=1/(4 N^(1/3)), theta=0.5, R1=4eps, R2=8eps, dt_s=1/128, n_hard=4; "
+                               "one call per step for all systems (CUDA graph), FP32 pairs, FP64 state"
+                               % (len(specs), total),
+                   "N_total": total, "systems": len(specs), "l2": "flushed (256 MiB write) before every timed step"},
+        "autotune": {"chosen": {"n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]},
+                     "est_ms_per_step": [round(float(x), 3) for x in table]},
+        "plain_fp64": {"value": v_p, "unit": METRIC, "ms_per_step": 1e3 * t_p,
+                       "form": "FP64 pairs, one system per hybrid_step call, same systems"},
+        "batched_over_plain": v_b / v_p,
+        "force_err_rms_vs_direct": {k: float(np.mean(v)) for k, v in errs.items()},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    ctx64.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
@@ -189,8 +287,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="single: one Plummer sphere (default); batched: the 512-system ensemble")
+    ap.add_argument("--c4-count", type=int, default=512)
     args = ap.parse_args()
     w = workload(args.n)
+    if args.workload == "batched" and args.impl == "gb300":
+        args.warmup = max(args.warmup, 3)
+        return run_c4(args)
     if args.impl == "reference":
         return run_reference(args, w)
     args.warmup = max(args.warmup, 3)

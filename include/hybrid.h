@@ -61,7 +61,12 @@ typedef enum {
  * threads_per_group: lanes that share one copy of a sink group in the FP32
  *          pair kernels; each lane then keeps ceil(n_crit / threads_per_group)
  *          sinks (1, 2 or 4) in registers. 0 = built-in default.
- * tile_depth: reserved tuning knob (0). */
+ * tile_depth: shared-memory staging depth of the FP32 far pair kernel: source
+ *          gathers run tile_depth - 1 tiles of 64 list entries ahead of their
+ *          use; 2, 3 or 4, 0 = built-in default (3).
+ * n_crit, threads_per_group and tile_depth change speed, not results beyond
+ * FP32 rounding order (n_crit also changes the groups and thus the lists);
+ * hybrid_autotune chooses them. */
 typedef struct {
     double G, eps, theta, R1, R2, dt_soft, a_err;
     int32_t n_hard, n_leaf, n_crit;
@@ -140,6 +145,19 @@ hybrid_status hybrid_step(hybrid_ctx *ctx, hybrid_system *sys, int n_soft_steps)
  * every kernel launch covers all systems. All systems share n_hard, n_leaf,
  * n_crit and precision; their other parameters may differ (params). */
 hybrid_status hybrid_step_batched(hybrid_ctx *ctx, hybrid_system *sys, int n_sys, int n_soft_steps);
+
+/* Autotuner (an implementation choice, not part of the method): for each
+ * candidate (n_crit, threads_per_group, tile_depth) -- cand holds n_cand
+ * triples; cand = NULL, n_cand = 0 uses a built-in list of 14 -- times one
+ * soft evaluation (tree build, walk, far and near pairs) and one hard
+ * evaluation (build, hard walk, near pairs) of the given systems with CUDA
+ * events after one untimed run, and estimates the time of a soft step as
+ * soft + (n_hard - 1) x hard. The fastest candidate becomes the context's
+ * setting for later calls. ms_out (optional, host, n_cand doubles) receives
+ * the estimates, best_out (optional) the index of the choice. The systems'
+ * arrays are read, not written. EINVAL for an invalid candidate. */
+hybrid_status hybrid_autotune(hybrid_ctx *ctx, hybrid_system *sys, int n_sys, const int32_t *cand, int n_cand,
+                              double *ms_out, int32_t *best_out);
 
 /* Copies the permutation of the last call into dev_perm (device int32, length
  * = total particles of that call): dev_perm[k] = index, in that call's input

@@ -106,6 +106,8 @@ bool params_ok(const hybrid_params *p, std::string *why)
     if (p->precision != 0 && p->precision != 1) return bad("precision must be 0 or 1");
     if (p->mac != 0 && p->mac != 1) return bad("mac must be 0 or 1");
     if (p->mac == 1 && !(p->a_err > 0.0)) return bad("a_err must be > 0 for the absolute MAC");
+    if (p->threads_per_group < 0) return bad("threads_per_group must be >= 0");
+    if (p->tile_depth != 0 && (p->tile_depth < 2 || p->tile_depth > 4)) return bad("tile_depth must be 0, 2, 3 or 4");
     return true;
 }
 
@@ -810,6 +812,79 @@ hybrid_status hybrid_step_batched(hybrid_ctx *c, hybrid_system *sys, int n_sys, 
 hybrid_status hybrid_step(hybrid_ctx *c, hybrid_system *sys, int n_soft_steps)
 {
     return hybrid_step_batched(c, sys, 1, n_soft_steps);
+}
+
+hybrid_status hybrid_autotune(hybrid_ctx *c, hybrid_system *sys, int n_sys, const int32_t *cand, int n_cand,
+                              double *ms_out, int32_t *best_out)
+{
+    static const int32_t defaults[][3] = {
+        {16, 4, 0},  {16, 8, 0},  {32, 8, 0},  {32, 16, 0}, {64, 16, 0},  {64, 32, 0}, {128, 32, 0}, {128, 64, 0},
+        {32, 8, 2},  {32, 8, 4},  {64, 16, 2}, {64, 16, 4}, {128, 32, 2}, {128, 32, 4}};
+    if (!c || !sys || n_sys < 1 || n_cand < 0 || (n_cand > 0 && !cand)) return HYBRID_EINVAL;
+    const int32_t *cv = n_cand > 0 ? cand : &defaults[0][0];
+    const int nc = n_cand > 0 ? n_cand : (int)(sizeof(defaults) / sizeof(defaults[0]));
+    const hybrid_params saved = c->p;
+    for (int i = 0; i < nc; ++i) {
+        hybrid_params q = saved;
+        q.n_crit = cv[3 * i];
+        q.threads_per_group = cv[3 * i + 1];
+        q.tile_depth = cv[3 * i + 2];
+        std::string why;
+        if (!params_ok(&q, &why)) {
+            set_err(c, "candidate %d: %s", i, why.c_str());
+            return HYBRID_EINVAL;
+        }
+    }
+    hybrid_status r = setup_batch(c, sys, n_sys, true);
+    if (r != HYBRID_OK) return r;
+    // the systems' own arrays are only read (copy-in); every candidate runs on the working copy
+    launch_copy_in(c, (const SysIO *)c->io_dev.p, false);
+    const std::vector<Op> soft = {simple(OP_BUILD), simple(OP_WALK, 3), simple(OP_PAIR_FAR), simple(OP_PAIR_NEAR, 3)};
+    const std::vector<Op> hard = {simple(OP_BUILD), simple(OP_WALK, 2), simple(OP_PAIR_NEAR, 2)};
+    cudaEvent_t ev[3];
+    for (int k = 0; k < 3; ++k)
+        if (cudaEventCreate(&ev[k]) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "event creation");
+    int best = -1;
+    double best_ms = 0.0;
+    for (int i = 0; i < nc && r == HYBRID_OK; ++i) {
+        c->p.n_crit = cv[3 * i];
+        c->p.threads_per_group = cv[3 * i + 1];
+        c->p.tile_depth = cv[3 * i + 2];
+        drop_graphs(c);   // captured launches carry the old choice
+        if ((r = run_ops(c, soft)) != HYBRID_OK || (r = run_ops(c, hard)) != HYBRID_OK) break;   // warm-up
+        cudaEventRecord(ev[0], c->st);
+        if ((r = run_ops(c, soft)) != HYBRID_OK) break;
+        cudaEventRecord(ev[1], c->st);
+        if ((r = run_ops(c, hard)) != HYBRID_OK) break;
+        cudaEventRecord(ev[2], c->st);
+        float t1 = 0.0f, t2 = 0.0f;
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t1, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t2, ev[1], ev[2]);
+        if (e != cudaSuccess) {
+            r = cuda_fail(c, e, "autotune timing");
+            break;
+        }
+        // one soft step = one soft evaluation + (n_hard - 1) hard evaluations (kicks do not depend on the choice)
+        const double ms = (double)t1 + (double)(c->p.n_hard - 1) * (double)t2;
+        if (ms_out) ms_out[i] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = i;
+            best_ms = ms;
+        }
+    }
+    for (int k = 0; k < 3; ++k) cudaEventDestroy(ev[k]);
+    c->p = saved;
+    if (r == HYBRID_OK && best >= 0) {
+        c->p.n_crit = cv[3 * best];
+        c->p.threads_per_group = cv[3 * best + 1];
+        c->p.tile_depth = cv[3 * best + 2];
+    }
+    drop_graphs(c);
+    c->tree_valid = false;
+    c->have_soft = c->have_hard = false;
+    if (best_out) *best_out = best;
+    return finish(c, r);
 }
 
 hybrid_status hybrid_get_perm(hybrid_ctx *c, int32_t *dev_perm)

@@ -164,11 +164,11 @@ static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
 constexpr uint32_t MULTI = 0x80000000u;
 
 // Raw sources (hi, lo float4 pairs of cells or particles) are gathered into a
-// ring of NST shared-memory stages with 16-byte cp.async copies issued
-// NST - 1 tiles ahead, from list indices loaded one tile before that; only
-// the rebasing to the group's reference point (one pass per staged entry,
-// by the lane that copied it) stands between a landed stage and its use.
-constexpr int NST = 3;
+// ring of NST shared-memory stages (the staging depth, 2 to 4; the near
+// kernel uses 3) with 16-byte cp.async copies issued NST - 1 tiles ahead,
+// from list indices loaded one tile before that; only the rebasing to the
+// group's reference point (one pass per staged entry, by the lane that copied
+// it) stands between a landed stage and its use.
 constexpr int PER = TILE / 32;
 
 // Rebased sources: the near kernel keeps {x, y, z, m} in tile[0, TILE); the
@@ -176,6 +176,7 @@ constexpr int PER = TILE / 32;
 // packed two-sink arithmetic, in tile[0, 2 PADT): entries from nt up to
 // PADT = TILE + 32 are zero-mass sources.
 constexpr int PADT = TILE + 32;
+template <int NST>
 struct WarpStage {
     float4 tile[2 * PADT];
     float4 rh[NST][TILE];     // raw hi parts (cells: nA, particles: phi)
@@ -207,7 +208,8 @@ struct ItemSrc {
         }
     }
     // gathers of tile t into stage t % NST; always closes one cp.async group
-    __device__ __forceinline__ void issue(const PairArgs &a, WarpStage &S, int t, int lane,
+    template <int NST>
+    __device__ __forceinline__ void issue(const PairArgs &a, WarpStage<NST> &S, int t, int lane,
                                           const uint32_t (&idx)[PER]) const
     {
         const int st = t % NST;
@@ -226,24 +228,27 @@ struct ItemSrc {
 
 // Runs the staging pipeline over the item's entries and calls
 // body(stage, nt) once per tile, after the tile has been rebased into S.tile.
-template <bool PACKED, typename Body>
-__device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, WarpStage &S, int lane, float crx,
-                                         float cry, float crz, Body &&body)
+template <bool PACKED, int NST, typename Body>
+__device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, WarpStage<NST> &S, int lane,
+                                         float crx, float cry, float crz, Body &&body)
 {
-    static_assert(NST == 3, "the prologue below is written for three stages");
+    static_assert(NST >= 2 && NST <= 4, "staging depth");
     const uint32_t ne = src.e1 - src.e0;
     const int ntile = (int)((ne + TILE - 1) / TILE);
     if (ntile == 0) return;
-    uint32_t i0[PER], i1[PER];
-    src.load_idx(a, 0, lane, i0);
-    src.load_idx(a, 1, lane, i1);
-    src.issue(a, S, 0, lane, i0);
-    src.issue(a, S, 1, lane, i1);
-    src.load_idx(a, 2, lane, i0);
+    {   // prologue: the indices of tiles 0 .. NST-2 are loaded together, then their gathers issued
+        uint32_t ip[NST - 1][PER];
+#pragma unroll
+        for (int t = 0; t < NST - 1; ++t) src.load_idx(a, t, lane, ip[t]);
+#pragma unroll
+        for (int t = 0; t < NST - 1; ++t) src.issue(a, S, t, lane, ip[t]);
+    }
+    uint32_t i0[PER];
+    src.load_idx(a, NST - 1, lane, i0);
     for (int t = 0; t < ntile; ++t) {
-        src.issue(a, S, t + 2, lane, i0);   // no copies past the end, but one group per tile
-        if (t + 3 < ntile) src.load_idx(a, t + 3, lane, i0);
-        cp_wait<NST - 1>();                 // this lane's copies of tile t have landed
+        src.issue(a, S, t + NST - 1, lane, i0);   // no copies past the end, but one group per tile
+        if (t + NST < ntile) src.load_idx(a, t + NST, lane, i0);
+        cp_wait<NST - 1>();                       // this lane's copies of tile t have landed
         const int st = t % NST;
         const int nt = (int)min((uint32_t)TILE, ne - (uint32_t)(t * TILE));
 #pragma unroll
@@ -344,8 +349,8 @@ __device__ __forceinline__ void body_far2(uint64_t X2, uint64_t Y2, uint64_t Z2,
 // lane runs the same number of rounds of two sources (entries from nt to
 // PADT are zero-mass sources), so the loop has no divergence; lanes outside
 // the copies compute sums that are never used. KP sink pairs per lane.
-template <int KP, bool GUARD>
-__device__ __forceinline__ void far_tile(const WarpStage &S, int nt, int copy, int copies, uint64_t E2,
+template <int KP, bool GUARD, int NST>
+__device__ __forceinline__ void far_tile(const WarpStage<NST> &S, int nt, int copy, int copies, uint64_t E2,
                                          const uint64_t (&SX)[KP], const uint64_t (&SY)[KP], const uint64_t (&SZ)[KP],
                                          uint64_t (&AX)[KP], uint64_t (&AY)[KP], uint64_t (&AZ)[KP])
 {
@@ -368,13 +373,13 @@ __device__ __forceinline__ void far_tile(const WarpStage &S, int nt, int copy, i
 
 // NEAR = false: cells + far particles -> soft. NEAR = true: near particles ->
 // soft (1 - K) and/or hard (K), by SOFT/HARD.
-template <int KS, bool NEAR, bool SOFT, bool HARD>
+template <int KS, bool NEAR, bool SOFT, bool HARD, int NST>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
 {
-    __shared__ WarpStage stages[PAIR_WARPS];
+    __shared__ WarpStage<NST> stages[PAIR_WARPS];
     if (a.st->code) return;
     const int lane = threadIdx.x & 31;
-    WarpStage &S = stages[threadIdx.x >> 5];
+    WarpStage<NST> &S = stages[threadIdx.x >> 5];
     for (int e = 2 * TILE + lane; e < 2 * PADT; e += 32) S.tile[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int64_t W = (int64_t)*a.nwork;
     unsigned long long inter = 0;
@@ -435,11 +440,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                 const uint64_t E2 = pk2(H.eps2, H.eps2);
                 if (H.eps2 > 0.0f)
                     pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
-                        far_tile<KP, false>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                        far_tile<KP, false, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
                     });
                 else   // eps = 0 without a hard part: a sink meets itself in its far particles
                     pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
-                        far_tile<KP, true>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                        far_tile<KP, true, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
                     });
 #pragma unroll
                 for (int p = 0; p < KP; ++p) {
@@ -715,10 +720,14 @@ void fill_args(hybrid_ctx *c, PairArgs &a)
     a.want_soft = a.want_hard = 0;
 }
 
+// staging depth: tile_depth (2, 3 or 4; 0 = 3) for the far kernel, 3 for the near kernel
 template <int KS, bool NEAR, bool SOFT, bool HARD>
 void go_f32(hybrid_ctx *c, const PairArgs &a)
 {
-    k_pair_f32<KS, NEAR, SOFT, HARD><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
+    const int depth = NEAR || c->p.tile_depth == 0 ? 3 : c->p.tile_depth;
+    if (!NEAR && depth == 2) k_pair_f32<KS, NEAR, SOFT, HARD, 2><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
+    else if (!NEAR && depth == 4) k_pair_f32<KS, NEAR, SOFT, HARD, 4><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
+    else k_pair_f32<KS, NEAR, SOFT, HARD, 3><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
 }
 
 // Sinks per lane KS = ceil(n_crit / threads_per_group), from 1 to 4; the

@@ -28,6 +28,7 @@ EXPORTS = (
     "hybrid_kick", "hybrid_drift", "hybrid_step", "hybrid_step_batched", "hybrid_get_perm", "hybrid_sync",
     "hybrid_last_error", "hybrid_tree_info", "hybrid_tree_copy", "hybrid_lists_copy", "hybrid_interactions",
     "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy", "hybrid_energy_noalloc",
+    "hybrid_autotune",
 )
 
 
@@ -93,6 +94,7 @@ def load() -> C.CDLL:
         "hybrid_profile_read": [ctx, C.c_int, P(D), P(I64), C.c_int],
         "hybrid_energy": [ctx, sysp, P(D), P(D)],
         "hybrid_energy_noalloc": [I64, VP, VP, VP, VP, VP, VP, VP, D, D, VP, P(D), P(D)],
+        "hybrid_autotune": [ctx, sysp, C.c_int, VP, C.c_int, VP, P(I32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -278,6 +280,30 @@ class Context:
 
     def hybrid_launch_count(self) -> int:
         return int(self.L.hybrid_launch_count(self.h))
+
+    def hybrid_autotune(self, systems, candidates=None):
+        """Runs the autotuner over `systems` (a System or a list); candidates is a
+        list of (n_crit, threads_per_group, tile_depth) or None for the built-in
+        list. Returns (chosen triple, estimated ms per soft step of every
+        candidate) and records the choice in self.params."""
+        systems = [systems] if isinstance(systems, System) else list(systems)
+        arr = (hybrid_system * len(systems))(*[s.c for s in systems])
+        if candidates is None:
+            cand, nc, nout = None, 0, 14
+        else:
+            flat = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32).reshape(-1, 3))
+            cand, nc, nout = flat, len(flat), len(flat)
+        ms = np.zeros(nout)
+        best = C.c_int32(-1)
+        self._check("hybrid_autotune", self.L.hybrid_autotune(
+            self.h, arr, len(systems), None if cand is None else cand.ctypes.data, nc, ms.ctypes.data, C.byref(best)))
+        defaults = [(16, 4, 0), (16, 8, 0), (32, 8, 0), (32, 16, 0), (64, 16, 0), (64, 32, 0), (128, 32, 0),
+                    (128, 64, 0), (32, 8, 2), (32, 8, 4), (64, 16, 2), (64, 16, 4), (128, 32, 2), (128, 32, 4)]
+        table = defaults if cand is None else [tuple(int(v) for v in row) for row in cand]
+        chosen = table[best.value]
+        self.params = dataclasses.replace(self.params, n_crit=chosen[0], threads_per_group=chosen[1],
+                                          tile_depth=chosen[2])
+        return chosen, ms
 
     def hybrid_energy(self, s: System):
         T, W = C.c_double(), C.c_double()

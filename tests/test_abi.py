@@ -47,6 +47,7 @@ def test_invalid_params_rejected_without_gpu(lib):
     bad = [
         dict(eps=-1.0), dict(R1=0.2, R2=0.1), dict(R1=0.1, R2=0.1), dict(n_hard=0), dict(n_leaf=0),
         dict(n_crit=0), dict(precision=2), dict(mac=1, a_err=0.0), dict(theta=-0.1),
+        dict(threads_per_group=-1), dict(tile_depth=1), dict(tile_depth=5),
     ]
     for kw in bad:
         p = hybrid.Params(**kw).c()
@@ -54,6 +55,7 @@ def test_invalid_params_rejected_without_gpu(lib):
         assert lib.hybrid_create(C.byref(h), C.byref(p), None) == hybrid.EINVAL, kw
         assert not h.value
     assert lib.hybrid_create(None, None, None) == hybrid.EINVAL
+    assert lib.hybrid_autotune(None, None, 0, None, 0, None, None) == hybrid.EINVAL
     assert lib.hybrid_destroy(None) == hybrid.OK
     assert lib.hybrid_launch_count(None) == 0
 

@@ -308,6 +308,38 @@ def test_batched_equals_alone(H, prec):
                 assert np.percentile(e, 99) <= 1e-5
 
 
+def test_autotune_choice_and_results(H):
+    sizes = [3000, 1200, 4100]
+    states = [ics.plummer(n, 40 + k) for k, n in enumerate(sizes)]
+    P = plummer_params(3000, 1)
+    ctx = H.Context(P)
+    sysb = [H.System(st, precision=1) for st in states]
+    before = [s.numpy() for s in sysb]
+    cands = [(32, 8, 0), (64, 16, 3), (64, 32, 2), (128, 32, 4)]
+    chosen, ms = ctx.hybrid_autotune(sysb, cands)
+    assert chosen in cands and np.all(ms > 0)
+    assert ms[cands.index(chosen)] == ms.min()
+    assert (ctx.params.n_crit, ctx.params.threads_per_group, ctx.params.tile_depth) == chosen
+    for b, s in zip(before, sysb):   # the autotuner only reads the systems
+        a = s.numpy()
+        for k in ("x", "y", "z", "vx", "vy", "vz", "m", "id"):
+            assert np.array_equal(a[k], b[k]), k
+    # a step with the tuned context equals one on a fresh context built with the chosen setting
+    ctx.hybrid_step_batched(sysb, 1)
+    P2 = H.Params(**{**P.__dict__, "n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]})
+    ref = [H.System(st, precision=1) for st in states]
+    H.Context(P2).hybrid_step_batched(ref, 1)
+    for s, r in zip(sysb, ref):
+        a, b = s.numpy(), r.numpy()
+        assert np.array_equal(a["id"], b["id"])
+        for w in ("s", "h"):
+            A = np.stack([a["a%s_%s" % (d, w)] for d in "xyz"], 1).astype(np.float64)
+            B = np.stack([b["a%s_%s" % (d, w)] for d in "xyz"], 1).astype(np.float64)
+            nz = np.linalg.norm(B, axis=1) > 0
+            e = np.linalg.norm(A - B, axis=1)[nz] / np.linalg.norm(B, axis=1)[nz]
+            assert np.percentile(e, 99) <= 1e-5
+
+
 def test_kick_drift_calls(H):
     st = ics.plummer(1000, 30)
     P = plummer_params(1000, 0)
