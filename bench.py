@@ -276,6 +276,122 @@ def run_c4(args):
     return 0
 
 
+def c5_trace(count, seed=5, rate=200.0):
+    """Served stream: Poisson arrivals at `rate` per second, N log-uniform in [2^12, 2^21], 32 soft steps."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, count))
+    sizes = np.floor(2.0 ** rng.uniform(12.0, 21.0, count)).astype(np.int64)
+    return arrivals, sizes
+
+
+def run_c5(args):
+    """Continuous batching (hybrid_server_*, FP32 form) on a Poisson request trace, wall-clock driven:
+    latency = completion - arrival per request; beside it the plain FP64 form serving the same trace
+    one request at a time (FIFO), from its measured per-request step rate."""
+    import numpy as np
+    import torch
+    from paper_1406_6158_gb300 import build as cuda_build
+    from paper_1406_6158_gb300 import hybrid, ics
+    cuda_build.build()
+    count, steps = args.c5_count, 32
+    arrivals, sizes = c5_trace(count)
+    tic = time.perf_counter()
+    states = [ics.plummer(int(n), 5 * 1000003 + k) for k, n in enumerate(sizes)]
+    log = (lambda *a: print("[served %.1fs]" % (time.perf_counter() - tic), *a, file=sys.stderr, flush=True)) \
+        if args.verbose else (lambda *a: None)
+    log("initial conditions ready: %d requests, %d particles" % (count, int(sizes.sum())))
+
+    def rparams(n, prec):
+        eps = 1.0 / (4.0 * float(n) ** (1.0 / 3.0))
+        return hybrid.Params(eps=eps, theta=0.5, R1=4 * eps, R2=8 * eps, dt_soft=1.0 / 128, n_hard=4,
+                             n_leaf=16, n_crit=128, threads_per_group=32, precision=prec)
+
+    budget = 150e9
+    srv = hybrid.Server(rparams(1 << 16, 1), budget)
+    # warm-up: one small request through the server (module load, first graph capture)
+    srv.submit(count, ics.plummer(4096, 1), rparams(4096, 1), 2)
+    while srv.next() is None:
+        srv.step()
+    log("warm-up done")
+    done, lat, k = 0, np.zeros(count), 0
+    busy_steps = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t_first = None
+    while done < count:
+        now = time.perf_counter() - t0
+        while k < count and arrivals[k] <= now:
+            srv.submit(k, states[k], rparams(sizes[k], 1), steps)
+            k += 1
+        a, q, f = srv.step()
+        if a == 0 and q == 0 and f == 0:
+            if k < count:
+                time.sleep(max(0.0, arrivals[k] - (time.perf_counter() - t0)))
+            continue
+        busy_steps += 1
+        if busy_steps % 20 == 0:
+            log("step %d: active %d queued %d finished %d done %d submitted %d, %.1f GB charged"
+                % (busy_steps, a, q, f, done, k, srv.used_bytes() / 1e9))
+        if time.perf_counter() - t0 > args.c5_max_seconds:
+            raise RuntimeError("served stream exceeded %.0f s" % args.c5_max_seconds)
+        if t_first is None:
+            t_first = now
+        while True:
+            r = srv.next()
+            if r is None:
+                break
+            lat[r[0]] = (time.perf_counter() - t0) - arrivals[r[0]]
+            done += 1
+    t_end = time.perf_counter() - t0
+    srv.close()
+    log("served: %.1f s, %d server steps" % (t_end, busy_steps))
+    work = float(sizes.sum()) * steps
+    served = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+              "mean_s": float(lat.mean()), "throughput": work / (t_end - arrivals[0]),
+              "server_steps": busy_steps}
+    # plain FP64, one request at a time: measured step rate of sampled requests, FIFO queue over the trace
+    ctx64 = hybrid.Context(rparams(1 << 16, 0))
+    rates = []
+    for j in np.linspace(0, count - 1, 3).astype(int):
+        s64 = hybrid.System(states[j], precision=0, ids=False, params=rparams(sizes[j], 0))
+        ctx64.hybrid_step(s64, 0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx64.hybrid_step(s64, 1)
+        e1.record()
+        torch.cuda.synchronize()
+        rates.append(float(sizes[j]) / (e0.elapsed_time(e1) / 1e3))
+        log("FP64 sample N=%d: %.3g particle-steps/s" % (sizes[j], rates[-1]))
+    ctx64.close()
+    rate64 = float(np.mean(rates))
+    t_free, lat64 = 0.0, np.zeros(count)
+    for i in range(count):
+        start = max(t_free, arrivals[i])
+        t_free = start + float(sizes[i]) * steps / rate64
+        lat64[i] = t_free - arrivals[i]
+    line = {
+        "metric": "served p50/p99 latency and particle-steps/s", "value": served["throughput"],
+        "unit": METRIC, "n_gpus": 1, "steps": steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "served stream: first %d requests of a Poisson trace at 200 req/s (seed 5), "
+                               "Plummer spheres with N log-uniform in [2^12, 2^21], 32 soft steps each, "
+                               "eps=1/(4 N^(1/3)), theta=0.5, R1=4eps, R2=8eps, dt_s=1/128, n_hard=4; "
+                               "admission by %d B per particle under a 150 GB budget; FP32 pairs, FP64 state"
+                               % (count, hybrid.SERVER_BYTES_PER_PARTICLE),
+                   "requests": count, "particles_total": int(sizes.sum()),
+                   "offered_particle_steps_per_s": work / float(arrivals[-1] - arrivals[0] + 1e-9)},
+        "served": served,
+        "serial_plain_fp64": {"p50_s": float(np.percentile(lat64, 50)), "p99_s": float(np.percentile(lat64, 99)),
+                              "throughput": rate64,
+                              "basis": "FP64 soft-step rate measured on 3 requests of the trace; FIFO, one "
+                                       "request at a time"},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -287,14 +403,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
-                    help="single: one Plummer sphere (default); batched: the 512-system ensemble")
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served"],
+                    help="single: one Plummer sphere (default); batched: the 512-system ensemble; "
+                         "served: the Poisson request stream")
     ap.add_argument("--c4-count", type=int, default=512)
+    ap.add_argument("--c5-count", type=int, default=100)
+    ap.add_argument("--c5-max-seconds", type=float, default=600.0)
+    ap.add_argument("--verbose", action="store_true")
     args = ap.parse_args()
     w = workload(args.n)
     if args.workload == "batched" and args.impl == "gb300":
         args.warmup = max(args.warmup, 3)
         return run_c4(args)
+    if args.workload == "served" and args.impl == "gb300":
+        return run_c5(args)
     if args.impl == "reference":
         return run_reference(args, w)
     args.warmup = max(args.warmup, 3)

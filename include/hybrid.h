@@ -215,6 +215,45 @@ int64_t hybrid_launch_count(hybrid_ctx *ctx);
  * (synchronises). Uses the context's eps and G (or sys->params). */
 hybrid_status hybrid_energy(hybrid_ctx *ctx, hybrid_system *sys, double *kinetic, double *potential);
 
+/* ---- serving: continuous batching of independent simulations ----
+ *
+ * Not part of the method: the paper advances one simulation at a time. A
+ * server owns one context (created with p; p->precision selects the form) and
+ * serves requests, each an independent system with its own parameters and
+ * number of soft steps:
+ *  - hybrid_server_submit copies a request's host state (FP64 arrays of
+ *    length n) and queues it under the caller's tag (>= 0); ETOOLARGE if
+ *    n x HYBRID_SERVER_BYTES_PER_PARTICLE exceeds the budget.
+ *  - hybrid_server_step admits queued requests in arrival order while the bytes
+ *    charged for the admitted ones (HYBRID_SERVER_BYTES_PER_PARTICLE per
+ *    particle: the request's device arrays and its share of the context's
+ *    working buffers) stay within budget_bytes; computes the first forces of
+ *    the newly admitted requests; advances every admitted request by one soft
+ *    step in one batched call (hybrid_step_batched); and retires the requests
+ *    whose steps are done (state back to host memory held by the server,
+ *    device arrays freed). It synchronises the stream; the counts returned are
+ *    those after the step.
+ *  - hybrid_server_next reports the oldest finished request: with all seven
+ *    arrays NULL it only sets tag and n (tag = -1 when none has finished);
+ *    with seven host arrays of length n it copies the final state, in the
+ *    request's input order, and forgets the request.
+ * A request's result does not depend on the other requests: bitwise in the
+ * FP64 form, to FP32 summation order in the FP32 form. One server is driven
+ * by one host thread. */
+#define HYBRID_SERVER_BYTES_PER_PARTICLE 1536
+typedef struct hybrid_server hybrid_server;
+hybrid_status hybrid_server_create(hybrid_server **srv, const hybrid_params *p, double budget_bytes, void *stream);
+hybrid_status hybrid_server_destroy(hybrid_server *srv);
+hybrid_status hybrid_server_submit(hybrid_server *srv, int64_t tag, int64_t n, const double *x, const double *y,
+                                   const double *z, const double *vx, const double *vy, const double *vz,
+                                   const double *m, const hybrid_params *params, int32_t n_steps);
+hybrid_status hybrid_server_step(hybrid_server *srv, int32_t *n_active, int32_t *n_queued, int32_t *n_finished);
+hybrid_status hybrid_server_next(hybrid_server *srv, int64_t *tag, int64_t *n, double *x, double *y, double *z,
+                                 double *vx, double *vy, double *vz, double *m);
+/* Bytes currently charged for admitted requests; text of the last failure. */
+double hybrid_server_used_bytes(hybrid_server *srv);
+const char *hybrid_server_last_error(hybrid_server *srv);
+
 /* ---- allocation-free entry point ----
  *
  * The paper has no counterpart to this call: it is an interface addition for

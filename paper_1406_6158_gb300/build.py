@@ -28,7 +28,7 @@ FLAGS = {
     "energy_static.cu": ["--fmad=false"],
     "pair.cu": ["-ftz=true", "-prec-sqrt=false", "-prec-div=false"],
 }
-SOURCES = ["hybrid_api.cu", "scan.cu", "tree.cu", "walk.cu", "pair.cu", "integrate.cu", "energy_static.cu"]
+SOURCES = ["hybrid_api.cu", "scan.cu", "tree.cu", "walk.cu", "pair.cu", "integrate.cu", "energy_static.cu", "serve.cu"]
 
 
 def nvcc() -> str:

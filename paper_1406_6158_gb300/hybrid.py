@@ -28,8 +28,10 @@ EXPORTS = (
     "hybrid_kick", "hybrid_drift", "hybrid_step", "hybrid_step_batched", "hybrid_get_perm", "hybrid_sync",
     "hybrid_last_error", "hybrid_tree_info", "hybrid_tree_copy", "hybrid_lists_copy", "hybrid_interactions",
     "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy", "hybrid_energy_noalloc",
-    "hybrid_autotune",
+    "hybrid_autotune", "hybrid_server_create", "hybrid_server_destroy", "hybrid_server_submit",
+    "hybrid_server_step", "hybrid_server_next", "hybrid_server_used_bytes", "hybrid_server_last_error",
 )
+SERVER_BYTES_PER_PARTICLE = 1536
 
 
 class hybrid_params(C.Structure):
@@ -95,6 +97,11 @@ def load() -> C.CDLL:
         "hybrid_energy": [ctx, sysp, P(D), P(D)],
         "hybrid_energy_noalloc": [I64, VP, VP, VP, VP, VP, VP, VP, D, D, VP, P(D), P(D)],
         "hybrid_autotune": [ctx, sysp, C.c_int, VP, C.c_int, VP, P(I32)],
+        "hybrid_server_create": [P(VP), P(hybrid_params), D, VP],
+        "hybrid_server_destroy": [VP],
+        "hybrid_server_submit": [VP, I64, I64, VP, VP, VP, VP, VP, VP, VP, P(hybrid_params), I32],
+        "hybrid_server_step": [VP, P(I32), P(I32), P(I32)],
+        "hybrid_server_next": [VP, P(I64), P(I64), VP, VP, VP, VP, VP, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -104,6 +111,10 @@ def load() -> C.CDLL:
     L.hybrid_last_error.restype = C.c_char_p
     L.hybrid_launch_count.argtypes = [ctx]
     L.hybrid_launch_count.restype = C.c_int64
+    L.hybrid_server_used_bytes.argtypes = [VP]
+    L.hybrid_server_used_bytes.restype = C.c_double
+    L.hybrid_server_last_error.argtypes = [VP]
+    L.hybrid_server_last_error.restype = C.c_char_p
     _lib = L
     return L
 
@@ -342,3 +353,67 @@ class Context:
             res.append((ent[o:o + a].copy(), ent[o + a:o + a + b].copy(), ent[o + a + b:o + a + b + c].copy()))
             o += a + b + c
         return res
+
+
+class Server:
+    """Continuous-batching server over the C-ABI (hybrid_server_*): requests are
+    host state dicts (FP64 x..m), each with its own Params and step count."""
+
+    FIELDS = ("x", "y", "z", "vx", "vy", "vz", "m")
+
+    def __init__(self, params: Params, budget_bytes: float, stream=None):
+        import torch
+        self.L = load()
+        self._cp = params.c()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        code = self.L.hybrid_server_create(C.byref(h), C.byref(self._cp), float(budget_bytes),
+                                           C.c_void_p(stream.cuda_stream))
+        if code != OK:
+            raise HybridError("hybrid_server_create", code, "")
+        self.h = h
+        self._keep = {}
+
+    def _check(self, func, code):
+        if code != OK:
+            raise HybridError(func, code, self.L.hybrid_server_last_error(self.h).decode(errors="replace"))
+
+    def submit(self, tag: int, state: dict, params: Params | None, n_steps: int):
+        arrs = [np.ascontiguousarray(state[k], dtype=np.float64) for k in self.FIELDS]
+        cp = params.c() if params is not None else None
+        self._check("hybrid_server_submit", self.L.hybrid_server_submit(
+            self.h, int(tag), len(arrs[0]), *[a.ctypes.data for a in arrs],
+            C.byref(cp) if cp is not None else None, int(n_steps)))
+
+    def step(self):
+        a, q, f = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check("hybrid_server_step", self.L.hybrid_server_step(self.h, C.byref(a), C.byref(q), C.byref(f)))
+        return a.value, q.value, f.value
+
+    def next(self):
+        """(tag, state dict in input order) of the oldest finished request, or None."""
+        tag, n = C.c_int64(), C.c_int64()
+        self._check("hybrid_server_next", self.L.hybrid_server_next(self.h, C.byref(tag), C.byref(n),
+                                                                     *([None] * 7)))
+        if tag.value < 0:
+            return None
+        out = {k: np.empty(n.value) for k in self.FIELDS}
+        self._check("hybrid_server_next", self.L.hybrid_server_next(
+            self.h, C.byref(tag), C.byref(n), *[out[k].ctypes.data for k in self.FIELDS]))
+        return tag.value, out
+
+    def used_bytes(self) -> float:
+        return float(self.L.hybrid_server_used_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.hybrid_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
