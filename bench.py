@@ -392,6 +392,80 @@ def run_c5(args):
     return 0
 
 
+def run_c3(args):
+    """Large single system: Hernquist sphere N=2^24 (seed 2, a=1, r<=100), eps=1/512, theta=0.4, R1=3eps,
+    R2=6eps, dt_s=1/128, n_hard=8, FP32 pairs on FP64 state."""
+    import numpy as np
+    import torch
+    from paper_1406_6158_gb300 import build as cuda_build
+    from paper_1406_6158_gb300 import hybrid, ics
+    cuda_build.build()
+    n = args.n if args.n != N_DEFAULT else 1 << 24
+    eps = 1.0 / 512
+    tic = time.perf_counter()
+    st = ics.hernquist(n, 2)
+    t_ic = time.perf_counter() - tic
+    P = hybrid.Params(eps=eps, theta=0.4, R1=3 * eps, R2=6 * eps, dt_soft=1.0 / 128, n_hard=8, n_leaf=16,
+                      n_crit=128, threads_per_group=32, precision=1)
+    stream = torch.cuda.current_stream()
+    ctx = hybrid.Context(P, stream)
+    s = hybrid.System(st, precision=1, ids=False)
+    ctx.hybrid_step(s, 0)
+    for _ in range(args.warmup):
+        ctx.hybrid_step(s, 1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.hybrid_profile(True)
+    for k in range(9):
+        ctx.hybrid_profile_read(k, reset=True)
+    launches0 = ctx.hybrid_launch_count()
+    clocks = ClockSampler(0)
+    inter_far = inter_near = 0
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        ctx.hybrid_step(s, 1)
+        ev[k][1].record(stream)
+        fi, ni = ctx.hybrid_interactions()
+        inter_far += fi
+        inter_near += ni
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.hybrid_launch_count() - launches0
+    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    kinds = [ctx.hybrid_profile_read(k) for k in range(9)]
+    ctx.hybrid_profile(False)
+    props = torch.cuda.get_device_properties(0)
+    sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
+    far_s = kinds[0][0] / 1e3 / max(kinds[0][1], 1)
+    achieved = FLOPS_PER_INTERACTION * inter_far / args.steps / far_s / 1e12
+    out = s.numpy()
+    a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+    a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+    ferr = force_error_rms(out, a_s, a_h, eps, nsample=256)
+    names = ["far_pair", "near_pair", "walk", "tree_build", "kick_drift", "sort", "topology", "moments", "groups"]
+    line = {
+        "metric": METRIC, "value": n * args.steps / t, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Hernquist sphere N=%d seed 2, a=1, r<=100, eps=1/512, theta=0.4, R1=3eps, "
+                               "R2=6eps, dt_s=1/128, n_hard=8; FP32 pairs, FP64 state" % n,
+                   "N": n, "l2": "inputs larger than L2", "ic_seconds": t_ic},
+        "interactions_per_s": (inter_far + P.n_hard * inter_near) / t,
+        "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
+        "hard_interactions_per_substep": inter_near / args.steps,
+        "force_err_rms_vs_direct": ferr,
+        "kernel_ms_per_step": {nm: kinds[k][0] / args.steps for k, nm in enumerate(names)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_pair_f32 far (cells + far particles, soft force)"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -403,9 +477,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "served"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large"],
                     help="single: one Plummer sphere (default); batched: the 512-system ensemble; "
-                         "served: the Poisson request stream")
+                         "served: the Poisson request stream; large: the 2^24 Hernquist sphere")
     ap.add_argument("--c4-count", type=int, default=512)
     ap.add_argument("--c5-count", type=int, default=100)
     ap.add_argument("--c5-max-seconds", type=float, default=600.0)
@@ -417,6 +491,8 @@ def main():
         return run_c4(args)
     if args.workload == "served" and args.impl == "gb300":
         return run_c5(args)
+    if args.workload == "large" and args.impl == "gb300":
+        return run_c3(args)
     if args.impl == "reference":
         return run_reference(args, w)
     args.warmup = max(args.warmup, 3)

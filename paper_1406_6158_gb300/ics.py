@@ -71,6 +71,15 @@ def _hernquist_df(E_rel: np.ndarray, Mh: float, a: float) -> np.ndarray:
 
 def hernquist(n: int, seed: int, a: float = 1.0, rmax: float = 100.0, chunk: int = 1 << 20) -> dict:
     """Hernquist sphere truncated at rmax, n equal-mass particles, total mass 1."""
+    return _hernquist(n, seed, a, rmax, chunk)[0]
+
+
+def hernquist_envelope(r: np.ndarray, a: float = 1.0, rmax: float = 100.0) -> np.ndarray:
+    """The rejection envelope the sampler uses at radii r (for checks)."""
+    return _hernquist(0, 0, a, rmax, 1 << 20, r)[1]
+
+
+def _hernquist(n, seed, a, rmax, chunk, env_at=None):
     rng = np.random.Generator(np.random.PCG64(seed))
     Xmax = (rmax / (rmax + a)) ** 2
     Mh = 1.0 / Xmax
@@ -78,15 +87,36 @@ def hernquist(n: int, seed: int, a: float = 1.0, rmax: float = 100.0, chunk: int
     r = a * sX / (1.0 - sX)
     pos = r[:, None] * _isotropic(rng, n)
     speed = np.empty(n)
-    vgrid = np.linspace(0.0, 1.0, 65)[1:]            # fractions of v_esc for the envelope
+    # fractions of v_esc for the envelope, geometric: near the centre the peak of v^2 f sits at v << v_esc
+    vgrid = np.geomspace(1e-6, 1.0, 512)
+
+    def envelope(rr):   # max over the v grid of v^2 f(Psi - v^2 / 2) at radii rr
+        psi = Mh / (rr + a)
+        vesc = np.sqrt(2.0 * psi)
+        g = (vgrid[None, :] * vesc[:, None]) ** 2 * _hernquist_df(
+            psi[:, None] - 0.5 * (vgrid[None, :] * vesc[:, None]) ** 2, Mh, a)
+        return g.max(axis=1)
+
+    # envelope tabulated on a log grid in r (ratio 1.005 between nodes); each particle takes 1.25 x the
+    # larger of its two bracketing nodes, and particles inside the first node get their own
+    rg = np.geomspace(1e-6 * a, rmax * (1 + 1e-9), 4096)
+    eg = envelope(rg)
+    if env_at is not None:
+        j = np.clip(np.searchsorted(rg, env_at) - 1, 0, rg.size - 2)
+        env = 1.25 * np.maximum(eg[j], eg[j + 1])
+        inner = env_at < rg[0]
+        if inner.any():
+            env[inner] = 1.25 * envelope(env_at[inner])
+        return None, env
     for c0 in range(0, n, chunk):
         rc = r[c0:c0 + chunk]
         psi = Mh / (rc + a)
         vesc = np.sqrt(2.0 * psi)
-        # envelope: 1.25 x the largest v^2 f over a 64-point grid in v
-        g = (vgrid[None, :] * vesc[:, None]) ** 2 * _hernquist_df(
-            psi[:, None] - 0.5 * (vgrid[None, :] * vesc[:, None]) ** 2, Mh, a)
-        env = 1.25 * g.max(axis=1)
+        j = np.clip(np.searchsorted(rg, rc) - 1, 0, rg.size - 2)
+        env = 1.25 * np.maximum(eg[j], eg[j + 1])
+        inner = rc < rg[0]
+        if inner.any():
+            env[inner] = 1.25 * envelope(rc[inner])
         out = np.empty(rc.size)
         todo = np.arange(rc.size)
         while todo.size:
@@ -97,7 +127,7 @@ def hernquist(n: int, seed: int, a: float = 1.0, rmax: float = 100.0, chunk: int
             todo = todo[~ok]
         speed[c0:c0 + chunk] = out
     vel = speed[:, None] * _isotropic(rng, n)
-    return _finish(pos, vel, n)
+    return _finish(pos, vel, n), None
 
 
 def ensemble_sizes(count: int, lo_log2: float, hi_log2: float, seed: int) -> np.ndarray:

@@ -441,6 +441,19 @@ def test_plummer_profile_and_virial():
     assert abs(T - 3 * math.pi / 64) < 0.01        # Plummer: T = -W/2 = 3 pi G M^2 / (64 a)
 
 
+def test_hernquist_envelope_bounds_target():
+    # the speed sampler is a rejection sampler: its envelope must bound v^2 f(Psi - v^2/2) for every v
+    from paper_1406_6158_gb300.ics import _hernquist_df
+    Mh = (101.0 / 100.0) ** 2
+    r = np.exp(np.random.default_rng(0).uniform(np.log(1e-7), np.log(100.0), 3000))
+    psi = Mh / (r + 1.0)
+    vesc = np.sqrt(2.0 * psi)
+    frac = np.concatenate([np.linspace(0.0, 1.0, 4001)[1:], np.geomspace(1e-8, 1.0, 4001)])
+    v = frac[None, :] * vesc[:, None]
+    target = (v * v * _hernquist_df(psi[:, None] - 0.5 * v * v, Mh, 1.0)).max(axis=1)
+    assert np.all(ics.hernquist_envelope(r) >= target)
+
+
 def test_hernquist_profile():
     s = ics.hernquist(20000, 2)
     r = np.sqrt(s["x"] ** 2 + s["y"] ** 2 + s["z"] ** 2)
