@@ -61,6 +61,29 @@ struct Chunk {
 };
 
 // Per-group data for the walk and pair kernels.
+// FP32 pair work item: the entry range [e0, e1) of one group's list, that
+// list being a cell run (entries e < Lc, at list[cbase + e]) followed by a
+// particle run (entries e >= Lc, at list[pbase + e]; pbase = start of the
+// particle run - Lc, modulo 2^64). Written by the single-pass walk.
+struct WorkItem {
+    uint64_t cbase, pbase;
+    uint32_t Lc, e0, e1, first;
+    uint32_t n;     // group size; bit 31 set when the group has several work items of this kind
+    uint32_t sys;
+};
+static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
+constexpr uint32_t ITEM_MULTI = 0x80000000u;
+constexpr int LCH_FAR = 512, LCH_NEAR = 256;
+
+// Entries per work item of a group of n sinks: lch for n >= 64, longer runs
+// (up to 8 lch) for smaller groups, so that items cost about the same
+// n x entries and a small group pays the per-item set-up less often.
+__host__ __device__ __forceinline__ uint64_t item_len(uint32_t n, int lch)
+{
+    const uint32_t f = n >= 64 ? 1u : (64u / (n > 0 ? n : 1u) < 8u ? 64u / (n > 0 ? n : 1u) : 8u);
+    return (uint64_t)lch * f;
+}
+
 struct GroupF {
     float4 c_hi;       // centre of the member box, hi part; w = half extent x
     float4 c_lo;       // centre lo part; w = half extent y
@@ -130,6 +153,8 @@ struct hybrid_ctx {
     hy::Buf gflag, gscan, gnode, gfirst, gcount, gsys, gF, glo, ghi, ngroups_dev;
     // lists
     hy::Buf lcnt, loff, list, stack, counter, io_dev, energy_dev, wstart, wmap;
+    hy::Buf wnear;                                 // near-pair work items (wmap holds the far ones)
+    int64_t capWork = 0;                           // work items per kind
     int last_walk_mode = 0;
 
     // profiling

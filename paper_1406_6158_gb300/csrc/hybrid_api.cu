@@ -9,6 +9,7 @@
 // (a build re-sorts already sorted particles into the same order, so it can
 // be repeated).
 #include <cmath>
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -160,6 +161,15 @@ bool alloc_nodes(hybrid_ctx *c, int64_t cap)
     return ok;
 }
 
+// FP32 pair work items (40 B each), far (wmap) and near (wnear)
+bool ensure_items(hybrid_ctx *c, int64_t n)
+{
+    if (n <= c->capWork) return true;
+    const bool ok = ensure(c, c->wmap, (size_t)n * sizeof(WorkItem)) && ensure(c, c->wnear, (size_t)n * sizeof(WorkItem));
+    if (ok) c->capWork = n;
+    return ok;
+}
+
 bool reserve(hybrid_ctx *c)
 {
     const int64_t N = c->N, S = c->S;
@@ -203,12 +213,14 @@ bool reserve(hybrid_ctx *c)
     // radix sort scratch: 64 tickets, digit counts [S][8][256], look-back words [8][chunks][256]
     ok = ok && ensure(c, c->hist, ((size_t)64 + (size_t)2048 * (S + c->nchunks)) * 4);
     if (c->capNodes < std::max<int64_t>(4096, N)) ok = ok && alloc_nodes(c, std::max<int64_t>(4096, N));
-    if (c->capList < std::max<int64_t>(1 << 20, 128 * N)) {
-        ok = ok && ensure(c, c->list, (size_t)std::max<int64_t>(1 << 20, 128 * N) * 4);
-        if (ok) c->capList = std::max<int64_t>(1 << 20, 128 * N);
+    // list entries: ~128 per particle, plus the unused tails of the regions the walking warps
+    // claim (three kinds of at most 2048 entries per warp)
+    const int64_t list0 = std::max<int64_t>(1 << 20, 128 * N) + (int64_t)3 * 2048 * c->walk_warps;
+    if (c->capList < list0) {
+        ok = ok && ensure(c, c->list, (size_t)list0 * 4);
+        if (ok) c->capList = list0;
     }
-    // pair work items (40 B each): at most one per group plus one per 256 list entries
-    ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 40);
+    ok = ok && ensure_items(c, 2 * c->capGroups + c->capList / 256 + 1024);
     if (c->capStack == 0) c->capStack = 4096;
     ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * c->capStack * 4);
     // scratch of the scans: the longest scan is over max(N, nodes, 3 groups + 1, tiles x 256)
@@ -552,8 +564,9 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
             const int64_t cap = s.need[1] + s.need[1] / 4 + 1024;
             ok = ok && ensure(c, c->list, (size_t)cap * 4);
             if (ok) c->capList = cap;
-            ok = ok && ensure(c, c->wmap, (size_t)(c->capGroups + c->capList / 256 + 2) * 40);
+            ok = ok && ensure_items(c, 2 * c->capGroups + c->capList / 256 + 1024);
         }
+        if (s.need[3] > c->capWork) ok = ok && ensure_items(c, s.need[3]);
         if (s.need[2] > c->capStack) {
             ok = ok && ensure(c, c->stack, (size_t)c->walk_warps * s.need[2] * 4);
             if (ok) c->capStack = s.need[2];
@@ -704,7 +717,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
                   &c->ncy, &c->ncz, &c->nB2, &c->nbmax, &c->nA, &c->nB, &c->ncrit, &c->ntopo, &c->nD, &c->nrb,
                   &c->nhr, &c->ndelta, &c->nside, &c->norg, &c->gflag, &c->gscan, &c->gnode, &c->gfirst, &c->gcount,
                   &c->gsys, &c->gF, &c->glo, &c->ghi, &c->ngroups_dev, &c->lcnt, &c->list, &c->stack, &c->counter,
-                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap, &c->nbig, &c->mitems, &c->mpart, &c->nbmax32};
+                  &c->io_dev, &c->energy_dev, &c->wstart, &c->wmap, &c->nbig, &c->mitems, &c->mpart, &c->nbmax32, &c->wnear};
     for (Buf *b : all)
         if (b->p) cudaFree(b->p);
     for (int f = 0; f < 7; ++f) {
@@ -983,13 +996,58 @@ hybrid_status hybrid_lists_copy(hybrid_ctx *c, int64_t *counts, int64_t *entries
     int64_t nn = 0, ng = 0;
     hybrid_status r = hybrid_tree_info(c, &nn, &ng);
     if (r != HYBRID_OK) return r;
+    const bool soft = c->last_walk_mode & 1, hard = (c->last_walk_mode >> 1) & 1;
+    if (c->p.precision == 1) {
+        // one-pass walk: a group's entries of each kind are the runs of its work items, in item order
+        uint64_t ctr[16];
+        if (cudaMemcpyAsync(ctr, c->counter.p, sizeof ctr, cudaMemcpyDeviceToHost, c->st) != cudaSuccess ||
+            cudaStreamSynchronize(c->st) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "list copy");
+        std::vector<WorkItem> itf, itn;
+        std::vector<uint32_t> gf, L;
+        if (!d2h(c, itf, c->wmap, (size_t)ctr[11]) || !d2h(c, itn, c->wnear, (size_t)ctr[12]) ||
+            !d2h(c, gf, c->gfirst, (size_t)ng) || !d2h(c, L, c->list, (size_t)ctr[10]) ||
+            cudaStreamSynchronize(c->st) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "list copy");
+        auto group_of = [&](uint32_t first) {
+            return (int64_t)(std::lower_bound(gf.begin(), gf.end(), first) - gf.begin());
+        };
+        std::vector<std::vector<uint32_t>> K[3];
+        for (auto &k : K) k.assign((size_t)ng, {});
+        for (const WorkItem &d : itf) {
+            const int64_t g = group_of(d.first);
+            for (uint32_t e = d.e0; e < d.e1; ++e)
+                K[e < d.Lc ? 0 : 1][(size_t)g].push_back(L[(e < d.Lc ? d.cbase : d.pbase) + e]);
+        }
+        for (const WorkItem &d : itn) {
+            const int64_t g = group_of(d.first);
+            for (uint32_t e = d.e0; e < d.e1; ++e) K[2][(size_t)g].push_back(L[d.pbase + e]);
+        }
+        int64_t need = 0;
+        for (int64_t g = 0; g < ng; ++g) {
+            counts[3 * g + 0] = soft ? (int64_t)K[0][g].size() : 0;
+            counts[3 * g + 1] = soft ? (int64_t)(K[1][g].size() + K[2][g].size()) : 0;
+            counts[3 * g + 2] = hard ? (int64_t)K[2][g].size() : 0;
+            need += counts[3 * g] + counts[3 * g + 1] + counts[3 * g + 2];
+        }
+        if (!entries) return HYBRID_OK;
+        if (need > cap_entries) return HYBRID_EINVAL;
+        int64_t o = 0;
+        for (int64_t g = 0; g < ng; ++g) {
+            if (soft)
+                for (int k = 0; k < 3; ++k)
+                    for (uint32_t v : K[k][g]) entries[o++] = v;
+            if (hard)
+                for (uint32_t v : K[2][g]) entries[o++] = v;
+        }
+        return HYBRID_OK;
+    }
     std::vector<uint64_t> off;
     if (!d2h(c, off, c->lcnt, 3 * ng + 1) || cudaStreamSynchronize(c->st) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "list copy");
     // stored as cells, far particles, near particles; reported as cells, soft
     // particles (far then near) and hard particles (near, when the walk asked for them)
     const uint64_t total = off[3 * ng];
-    const bool soft = c->last_walk_mode & 1, hard = (c->last_walk_mode >> 1) & 1;
     int64_t need = 0;
     for (int64_t g = 0; g < ng; ++g) {
         const int64_t nc = (int64_t)(off[g + 1] - off[g]), nf = (int64_t)(off[ng + g + 1] - off[ng + g]),

@@ -6,12 +6,12 @@
 //   near particles: the only pairs where K can be non-zero; one pass adds
 //     F (1 - K) to the soft force and F K to the hard force ("near" kernel).
 //
-// FP32 form. Work item = (group, chunk of at most lch consecutive entries of
-// one of the group's lists), pulled from a global counter. One warp per work
-// item: sources are staged, 64 at a time, into the warp's shared-memory tile
-// as float4 {x, y, z, m} relative to the group's reference point (the hi part
-// of its first sink: on the hi grid, so hi - c is exact); the next tile's
-// gathers are issued before the current tile is used. A group of n sinks uses
+// FP32 form. Work item = (group, run of at most item_len consecutive entries
+// of one of the group's lists), written by the walk and pulled from a global
+// counter. One warp per work item: sources are staged, 64 at a time, into the
+// warp's shared-memory tile as float4 {x, y, z, m} relative to the group's
+// reference point (the hi part of its first sink: on the hi grid, so hi - c
+// is exact); the gathers run ahead of their use (see the staging ring). A group of n sinks uses
 // lpc = ceil(n / KS) lanes per copy with KS sinks per lane in registers, and
 // copies = 32 / lpc copies of the group split the sources (source j goes to
 // copy j mod copies) and are added at the end. A group with one chunk stores
@@ -29,9 +29,6 @@ namespace {
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_WARPS = PAIR_THREADS / 32;
 constexpr int TILE = 64;
-constexpr int LCH_FAR = 512, LCH_NEAR = 256;
-
-struct WorkItem;
 
 struct PairArgs {
     const int64_t *ngroups;
@@ -45,10 +42,9 @@ struct PairArgs {
     unsigned long long *counter;
     unsigned long long *inter_soft, *inter_hard;   // pairs of the far kernel / of the near kernel
     const Status *st;
-    // work items: chunks of at most lch list entries of one group
+    // FP32 work items (see WorkItem) and their number
     const WorkItem *items;
     const uint64_t *nwork;
-    int lch;
     int want_soft, want_hard;
 };
 
@@ -150,18 +146,7 @@ __device__ __forceinline__ int64_t next_item(unsigned long long *counter, int la
 // ---------------------------------------------------------------------------
 // FP32 work items and source staging
 // ---------------------------------------------------------------------------
-// A work item is the entry range [e0, e1) of one group's list, that list being
-// the group's cell run (entries e < Lc, at list[cbase + e]) followed by its
-// particle run (entries e >= Lc, at list[pbase + e] with pbase = start of the
-// particle run - Lc, modulo 2^64). The near lists have no cell run (Lc = 0).
-struct WorkItem {
-    uint64_t cbase, pbase;
-    uint32_t Lc, e0, e1, first;
-    uint32_t n;     // group size; bit 31 set when the group has several work items
-    uint32_t sys;
-};
-static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
-constexpr uint32_t MULTI = 0x80000000u;
+constexpr uint32_t MULTI = ITEM_MULTI;
 
 // Raw sources (hi, lo float4 pairs of cells or particles) are gathered into a
 // ring of NST shared-memory stages (the staging depth, 2 to 4; the near
@@ -530,72 +515,6 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
     if (lane == 0) atomicAdd(NEAR ? a.inter_hard : a.inter_soft, inter);
 }
 
-// Entries per work item of a group of n sinks: lch for n >= 64, longer runs
-// (up to 8 lch) for smaller groups, so that items cost about the same
-// n x entries and a small group pays the per-item set-up less often.
-__device__ __forceinline__ uint64_t item_len(uint32_t n, int lch)
-{
-    const uint32_t f = n >= 64 ? 1u : min(8u, 64u / max(n, 1u));
-    return (uint64_t)lch * f;
-}
-
-// work items per group: max(1, ceil(list length / item_len))
-__global__ void __launch_bounds__(256) k_pair_plan(const int64_t *__restrict__ ngroups,
-                                                   const uint64_t *__restrict__ off,
-                                                   const uint32_t *__restrict__ gcount, int near, int lch,
-                                                   uint32_t *__restrict__ wcount, const Status *st)
-{
-    if (st->code) return;
-    const int64_t ng = *ngroups;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t L = near ? (off[2 * ng + g + 1] - off[2 * ng + g])
-                                : (off[g + 1] - off[g]) + (off[ng + g + 1] - off[ng + g]);
-        const uint64_t len = item_len(gcount[g], lch);
-        wcount[g] = (uint32_t)max((uint64_t)1, (L + len - 1) / len);
-    }
-}
-
-// the work items of every group, from the scanned item counts
-__global__ void __launch_bounds__(256) k_pair_map(const int64_t *__restrict__ ngroups, uint32_t *__restrict__ wstart,
-                                                  const uint64_t *__restrict__ total, const uint64_t *__restrict__ off,
-                                                  const uint32_t *__restrict__ gfirst,
-                                                  const uint32_t *__restrict__ gcount,
-                                                  const uint32_t *__restrict__ gsys, int near, int lch,
-                                                  WorkItem *__restrict__ items, const Status *st)
-{
-    if (st->code) return;
-    const int64_t ng = *ngroups;
-    const uint32_t T = (uint32_t)*total;
-    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t s0 = wstart[g];
-        const uint32_t s1 = (g + 1 < ng) ? wstart[g + 1] : T;
-        uint64_t c0 = 0, Lc = 0, p0, L;
-        if (near) {
-            p0 = off[2 * ng + g];
-            L = off[2 * ng + g + 1] - p0;
-        } else {
-            c0 = off[g];
-            Lc = off[g + 1] - c0;
-            p0 = off[ng + g];
-            L = Lc + (off[ng + g + 1] - p0);
-        }
-        WorkItem d;
-        d.cbase = c0;
-        d.pbase = p0 - Lc;
-        d.Lc = (uint32_t)Lc;
-        d.first = gfirst[g];
-        d.n = gcount[g] | (s1 - s0 > 1 ? MULTI : 0u);
-        d.sys = gsys[g];
-        const uint64_t len = item_len(gcount[g], lch);
-        for (uint32_t w = s0; w < s1; ++w) {
-            const uint64_t e0 = (uint64_t)(w - s0) * len;
-            d.e0 = (uint32_t)e0;
-            d.e1 = (uint32_t)min(L, e0 + len);
-            items[w] = d;
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------
 // FP64 kernel: one warp per group, one lane per sink (rounds of 32 sinks),
 // sources staged as double4 in shared memory.
@@ -716,7 +635,6 @@ void fill_args(hybrid_ctx *c, PairArgs &a)
     a.st = status_dev(c);
     a.items = nullptr;
     a.nwork = nullptr;
-    a.lch = 0;
     a.want_soft = a.want_hard = 0;
 }
 
@@ -765,17 +683,9 @@ void launch_pairs(hybrid_ctx *c, bool near, int mode)
         else k_pair_f64<false><<<c->nsm * 12, PAIR_THREADS, 0, c->st>>>(a);
         c->launches++;
     } else {
-        const int lch = near ? LCH_NEAR : LCH_FAR;
-        uint32_t *wstart = (uint32_t *)c->wstart.p;
-        uint64_t *d_total = (uint64_t *)c->counter.p + 8;
-        const int gridg = (int)std::max<int64_t>(1, std::min<int64_t>((c->capGroups + 255) / 256, c->nsm * 8));
-        k_pair_plan<<<gridg, 256, 0, c->st>>>(a.ngroups, a.off, a.gcount, near ? 1 : 0, lch, wstart, st);
-        scan_u32(c, wstart, 0, a.ngroups, c->capGroups, d_total);
-        k_pair_map<<<gridg, 256, 0, c->st>>>(a.ngroups, wstart, d_total, a.off, a.gfirst, a.gcount, a.gsys,
-                                             near ? 1 : 0, lch, (WorkItem *)c->wmap.p, st);
-        a.items = (const WorkItem *)c->wmap.p;
-        a.nwork = d_total;
-        a.lch = lch;
+        // work items written by the one-pass walk: far ones in wmap, near ones in wnear
+        a.items = (const WorkItem *)(near ? c->wnear.p : c->wmap.p);
+        a.nwork = (const uint64_t *)c->counter.p + (near ? 12 : 11);
         if (!near)
             for (int d = 0; d < 3; ++d) cudaMemsetAsync(c->acc_s[d].p, 0, (size_t)c->N * sizeof(float), c->st);
         if (near && a.want_hard)
@@ -784,7 +694,7 @@ void launch_pairs(hybrid_ctx *c, bool near, int mode)
         else if (a.want_soft && a.want_hard) go_ks<true, true, true>(c, a);
         else if (a.want_soft) go_ks<true, true, false>(c, a);
         else go_ks<true, false, true>(c, a);
-        c->launches += 3;
+        c->launches += 1;
     }
     prof_end(c, kind, e0);
 }

@@ -13,8 +13,17 @@
 //                   soft or the hard walk: the only pairs where K can be
 //                   non-zero (soft weight 1 - K, hard weight K),
 // and pushes the children of opened cells. r is the distance from the cell's
-// centre of mass to the group box. The count pass sizes every list, a scan
-// turns counts into offsets, and the fill pass writes the lists.
+// centre of mass to the group box.
+//
+// FP32 form (one pass): each warp writes the three kinds of entries into
+// regions of the list buffer it claims with an atomic add (at least
+// WALK_REGION entries per kind at a time), so a group's entries of one kind
+// are contiguous until a region runs out; every contiguous run becomes pair
+// work items of at most item_len entries, appended to the far (cells, far
+// particles) or near item array, which the pair kernels consume directly.
+// FP64 form (two passes): the count pass sizes every list, a scan turns
+// counts into offsets, and the fill pass writes them (one list per group and
+// kind, for the deterministic FP64 pair kernel).
 #include "hy_internal.cuh"
 
 namespace hy {
@@ -46,7 +55,15 @@ struct WalkArgs {
     int mode;
     Status *st;
     int where;
+    // one-pass form
+    const uint32_t *gfirst, *gcount;
+    unsigned long long *list_cursor;     // next free list entry
+    unsigned long long *item_count;      // [0] far items, [1] near items
+    WorkItem *items_far, *items_near;
+    int64_t cap_items;
 };
+
+constexpr uint32_t WALK_REGION = 2048;
 
 __device__ __forceinline__ void fail(Status *st, int code, int where)
 {
@@ -244,6 +261,202 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(WalkArgs a)
     }
 }
 
+// Work items of one contiguous run [start, start + len) of a group's entries
+// of kind t (0 cells, 1 far particles, 2 near particles); all lanes call it.
+__device__ __forceinline__ bool emit_items(const WalkArgs &a, int t, uint64_t start, uint64_t len, uint32_t first,
+                                           uint32_t n, uint32_t sys, bool multi, int lane)
+{
+    const int cls = t == 2 ? 1 : 0;
+    const uint64_t per = item_len(n, t == 2 ? LCH_NEAR : LCH_FAR);
+    const uint64_t m = (len + per - 1) / per;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(a.item_count + cls, (unsigned long long)m);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)(base + m) > a.cap_items) return false;
+    WorkItem *dst = (cls ? a.items_near : a.items_far) + base;
+    for (uint64_t j = lane; j < m; j += 32) {
+        WorkItem d;
+        d.cbase = t == 0 ? start : 0;
+        d.pbase = t == 0 ? 0 : start;
+        d.Lc = t == 0 ? (uint32_t)len : 0u;
+        d.e0 = (uint32_t)(j * per);
+        d.e1 = (uint32_t)min(len, (j + 1) * per);
+        d.first = first;
+        d.n = n | (multi ? ITEM_MULTI : 0u);
+        d.sys = sys;
+        dst[j] = d;
+    }
+    return true;
+}
+
+// FP32 form of the walk in one pass (see the top of the file). The warp's
+// region and open-run state of kind t (0 cells, 1 far, 2 near particles)
+// lives on lane t and is broadcast when needed.
+__global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
+{
+    Status *st = a.st;
+    if (st->code) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const int64_t ng = *a.ngroups;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    uint32_t *stk = a.stack + gw * a.cap_stack;
+    const bool want_soft = a.mode & 1, want_hard = (a.mode >> 1) & 1;
+    uint64_t my_cur = 0, my_end = 0, my_start = 0, my_len = 0;   // kind = lane (lanes 0..2)
+    bool fail_list = false, fail_items = false, overflow = false;
+
+    for (;;) {
+        unsigned long long gg = 0;
+        if (lane == 0) gg = atomicAdd(a.counter, 1ull);
+        const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gg, 0);
+        if (g >= ng) break;
+        const uint32_t s = a.gsys[g];
+        const bool has_hard = a.sp[s].has_hard != 0;
+        const bool wh0 = want_hard && has_hard;
+        const uint32_t gfirst = a.gfirst[g], gn = a.gcount[g];
+        const GroupF G = a.gF[g];
+        const float cx = G.c_hi.x, cy = G.c_hi.y, cz = G.c_hi.z, hx = G.c_hi.w;
+        const float lx = G.c_lo.x, ly = G.c_lo.y, lz = G.c_lo.z, hy = G.c_lo.w, hz = G.hz_root.x;
+        my_start = my_cur;
+        my_len = 0;
+        uint32_t early_far = 0, early_near = 0;   // items already emitted for this group
+        int64_t sp = 0;
+        if (want_soft || wh0) {
+            if (lane == 0) stk[0] = a.sysroot[s] | ((uint32_t)want_soft << 30) | ((uint32_t)wh0 << 31);
+            sp = 1;
+        }
+        __syncwarp();
+        // position for tot more entries of kind t, or ~0 on failure; closes the open run and claims a
+        // new region when the current one is too small
+        auto reserve = [&](int t, uint64_t tot) -> uint64_t {
+            const uint64_t cur = __shfl_sync(0xffffffffu, my_cur, t), end = __shfl_sync(0xffffffffu, my_end, t);
+            if (cur + tot <= end) return cur;
+            const uint64_t len = __shfl_sync(0xffffffffu, my_len, t), st0 = __shfl_sync(0xffffffffu, my_start, t);
+            if (len > 0) {
+                if (!emit_items(a, t, st0, len, gfirst, gn, s, true, lane)) {
+                    fail_items = true;
+                    return ~0ull;
+                }
+                const uint64_t per = item_len(gn, t == 2 ? LCH_NEAR : LCH_FAR);
+                (t == 2 ? early_near : early_far) += (uint32_t)((len + per - 1) / per);
+            }
+            const uint64_t size = tot > WALK_REGION ? tot : WALK_REGION;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(a.list_cursor, (unsigned long long)size);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if ((int64_t)(base + size) > a.cap_list) {
+                fail_list = true;
+                return ~0ull;
+            }
+            if (lane == t) {
+                my_cur = base;
+                my_end = base + size;
+                my_start = base;
+                my_len = 0;
+            }
+            return base;
+        };
+        while (sp > 0) {
+            const int take = (int)(sp < 32 ? sp : 32);
+            uint32_t e = 0;
+            if (lane < take) e = stk[sp - take + lane];
+            sp -= take;
+            __syncwarp();
+            const bool valid = lane < take;
+            const uint32_t c = e & 0x3fffffffu;
+            const bool ws = (e >> 30) & 1u, wh = (e >> 31) & 1u;
+            bool accept = false, near = false;
+            uint4 T = make_uint4(NONE, 0, 0, 0);
+            if (valid) {
+                T = a.topo[c];
+                const float4 A = a.nA[c], B = a.nB[c];
+                const float2 cr = a.crit[c];
+                const float rx = fmaxf(fabsf((A.x - cx) + (B.x - lx)) - hx, 0.0f);
+                const float ry = fmaxf(fabsf((A.y - cy) + (B.y - ly)) - hy, 0.0f);
+                const float rz = fmaxf(fabsf((A.z - cz) + (B.z - lz)) - hz, 0.0f);
+                const float d2 = rx * rx + ry * ry + rz * rz;
+                accept = d2 >= cr.x;
+                near = has_hard && (d2 < cr.y);
+            }
+            const bool leaf = (T.y == 0);
+            const bool open_s = ws && !accept;
+            const bool open_h = wh && near;
+            const bool take_cell = valid && ws && accept;
+            const bool soft_leaf = valid && leaf && open_s && !near;
+            const bool hard_leaf = valid && leaf && (open_s || open_h) && near;
+            const bool open = valid && !leaf && (open_s || open_h);
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {   // cells, far particles, near particles
+                const bool on = t == 0 ? take_cell : (t == 1 ? soft_leaf : hard_leaf);
+                uint32_t tot;
+                const uint32_t k = on ? (t == 0 ? 1u : T.w) : 0u;
+                const uint32_t ex = warp_excl_scan(k, tot);
+                if (tot) {
+                    const uint64_t pos = reserve(t, tot);
+                    if (pos == ~0ull) break;
+                    if (on) {
+                        uint32_t *dst = a.list + pos + ex;
+                        if (t == 0) dst[0] = c;
+                        else
+                            for (uint32_t j = 0; j < k; ++j) dst[j] = T.z + j;
+                    }
+                    if (lane == t) {
+                        my_cur = pos + tot;
+                        my_len += tot;
+                    }
+                }
+            }
+            if (fail_list || fail_items) break;
+            {   // children of opened cells
+                uint32_t tot;
+                const uint32_t k = open ? T.y : 0u;
+                const uint32_t ex = warp_excl_scan(k, tot);
+                if (sp + (int64_t)tot > a.cap_stack) {
+                    overflow = true;
+                    break;
+                }
+                if (open) {
+                    const uint32_t fl = ((uint32_t)open_s << 30) | ((uint32_t)open_h << 31);
+                    for (uint32_t j = 0; j < k; ++j) stk[sp + ex + j] = (T.x + j) | fl;
+                }
+                sp += tot;
+            }
+            __syncwarp();
+        }
+        if (overflow || fail_list || fail_items) break;
+        // the group's final runs: several items of one kind add atomically, a single one stores
+        uint64_t len3[3], st3[3];
+        uint32_t fin_far = early_far, fin_near = early_near;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            len3[t] = __shfl_sync(0xffffffffu, my_len, t);
+            st3[t] = __shfl_sync(0xffffffffu, my_start, t);
+            const uint64_t per = item_len(gn, t == 2 ? LCH_NEAR : LCH_FAR);
+            (t == 2 ? fin_near : fin_far) += (uint32_t)((len3[t] + per - 1) / per);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (len3[t] > 0 && !fail_items)
+                if (!emit_items(a, t, st3[t], len3[t], gfirst, gn, s, (t == 2 ? fin_near : fin_far) > 1, lane))
+                    fail_items = true;
+        if (fail_items) break;
+    }
+    if (lane == 0) {
+        if (overflow) {
+            fail(st, HYBRID_ECAPACITY, a.where);
+            st->need[2] = 2 * a.cap_stack;
+        }
+        if (fail_list) {
+            fail(st, HYBRID_ECAPACITY, a.where);
+            atomicMax((unsigned long long *)&st->need[1], (unsigned long long)(2 * a.cap_list));
+        }
+        if (fail_items) {
+            fail(st, HYBRID_ECAPACITY, a.where);
+            atomicMax((unsigned long long *)&st->need[3], (unsigned long long)(2 * a.cap_items));
+        }
+    }
+}
+
 }  // namespace
 
 void launch_walk(hybrid_ctx *c, int mode)
@@ -277,19 +490,34 @@ void launch_walk(hybrid_ctx *c, int mode)
     a.mode = mode;
     a.st = st;
     a.where = c->op;
+    a.gfirst = (const uint32_t *)c->gfirst.p;
+    a.gcount = (const uint32_t *)c->gcount.p;
+    a.list_cursor = (unsigned long long *)c->counter.p + 10;
+    a.item_count = (unsigned long long *)c->counter.p + 11;
+    a.items_far = (WorkItem *)c->wmap.p;
+    a.items_near = (WorkItem *)c->wnear.p;
+    a.cap_items = c->capWork;
     const int grid = c->walk_warps * 32 / WALK_THREADS;
     cudaEvent_t e0 = nullptr;
     prof_begin(c, PROF_WALK, &e0);
+    if (c->p.precision == 1) {   // one pass: the group counter, the list cursor and the item counts start at 0
+        cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned long long), c->st);
+        cudaMemsetAsync((unsigned long long *)c->counter.p + 10, 0, 3 * sizeof(unsigned long long), c->st);
+        a.counter = (unsigned long long *)c->counter.p;
+        k_walk1<<<grid, WALK_THREADS, 0, c->st>>>(a);
+        prof_end(c, PROF_WALK, e0);
+        c->launches += 1;
+        c->last_walk_mode = mode;
+        return;
+    }
     // count pass
     cudaMemsetAsync(c->counter.p, 0, 2 * sizeof(unsigned long long), c->st);
     a.counter = (unsigned long long *)c->counter.p;
-    if (c->p.precision == 0) k_walk<true, false><<<grid, WALK_THREADS, 0, c->st>>>(a);
-    else k_walk<false, false><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    k_walk<true, false><<<grid, WALK_THREADS, 0, c->st>>>(a);
     scan_u64(c, (uint64_t *)c->lcnt.p, 0, d_n3, 3 * c->capGroups, d_total);
     // fill pass
     a.counter = (unsigned long long *)c->counter.p + 1;
-    if (c->p.precision == 0) k_walk<true, true><<<grid, WALK_THREADS, 0, c->st>>>(a);
-    else k_walk<false, true><<<grid, WALK_THREADS, 0, c->st>>>(a);
+    k_walk<true, true><<<grid, WALK_THREADS, 0, c->st>>>(a);
     prof_end(c, PROF_WALK, e0);
     c->launches += 2;
     c->last_walk_mode = mode;
