@@ -480,6 +480,8 @@ def main():
     ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large"],
                     help="single: one Plummer sphere (default); batched: the 512-system ensemble; "
                          "served: the Poisson request stream; large: the 2^24 Hernquist sphere")
+    ap.add_argument("--tune", default="auto",
+                    help="auto (autotuner) or n_crit,threads_per_group,tile_depth for the single workload")
     ap.add_argument("--c4-count", type=int, default=512)
     ap.add_argument("--c5-count", type=int, default=100)
     ap.add_argument("--c5-max-seconds", type=float, default=600.0)
@@ -524,6 +526,11 @@ def main():
     ctx = hybrid.Context(P, stream)
     st = ics.plummer(w["n"], w["seed"])
     s = hybrid.System(st, precision=1)
+    if args.tune == "auto":
+        chosen, _ = ctx.hybrid_autotune(s)     # n_crit, threads per group, staging depth (untimed)
+    else:                                      # a fixed choice, e.g. to profile the autotuned configuration
+        chosen = tuple(int(v) for v in args.tune.split(","))
+        ctx.hybrid_autotune(s, [chosen])
     ctx.hybrid_step(s, 0)                      # forces at the initial positions
     for _ in range(args.warmup):
         ctx.hybrid_step(s, 1)
@@ -620,7 +627,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(w), "N": w["n"], "parallelism": "replicas x%d" % ws,
-                       "l2": "flushed (256 MiB write) before every timed step", "state": "f64"},
+                       "l2": "flushed (256 MiB write) before every timed step", "state": "f64",
+                       "autotuned": {"n_crit": chosen[0], "threads_per_group": chosen[1],
+                                     "tile_depth": chosen[2]}},
             # soft force: far + near pairs once per step; hard force: near pairs at each of the n_hard sub-steps
             "interactions_per_s": ws * (inter_far + w["n_hard"] * inter_near) / t_steps,
             "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
