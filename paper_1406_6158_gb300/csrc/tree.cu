@@ -9,6 +9,7 @@
 // particle range and radix tile stays inside one system.
 #include "hy_internal.cuh"
 
+#include <cuda/atomic>
 #include <cstdio>
 #include <type_traits>
 
@@ -619,10 +620,14 @@ __global__ void __launch_bounds__(256) k_nodes_b(const uint64_t *__restrict__ to
 }
 
 // ---------------------------------------------------------------------------
-// Moments, bottom-up. A leaf sums its particles; the last child to finish
-// (counted with an atomic) sums the children into the parent. FP64.
-// B2 of a parent by the parallel-axis rule: sum_c [B2_c + M_c |com_c - com|^2].
-// Also writes the FP32 hi/lo copy of the centre of mass (walk and pair data).
+// Moments. A cell of at most MOM_CH particles sums its own particle range
+// (one warp): M, centre of mass, B2 and b_max, with no wait on other cells.
+// A larger cell is combined from its children by the last of them to finish
+// (counted with an atomic; no wait anywhere): M = sum M_j, COM = sum M_j
+// COM_j / M, B2 = sum_j [B2_j + M_j |COM_j - COM|^2] (parallel axis, no
+// cancellation), in a fixed order. b_max of a larger cell is the largest
+// distance of its particles to its centre of mass, taken afterwards over
+// chunks of BM_CH particles with one atomic max per chunk.
 // ---------------------------------------------------------------------------
 struct MomArgs {
     const uint32_t *lvl, *nfirst, *ncount, *nnch, *nchild, *nparent, *nlevel;
@@ -632,8 +637,10 @@ struct MomArgs {
     const SysBox *box;
     double *M, *cx, *cy, *cz, *B2;
     float4 *nA, *nB;
-    uint32_t *done, *leafof;
+    uint32_t *done;
     const float4 *phi, *plo;
+    unsigned long long *bmax64;   // FP64 form: b_max as FP64 bits
+    unsigned int *bmax32;         // FP32 form: b_max as FP32 bits
 };
 
 __device__ __forceinline__ uint32_t digit_at(uint64_t key, int lev)
@@ -734,22 +741,29 @@ __device__ __forceinline__ void mom_store_f32(const MomArgs &a, uint32_t c, uint
 }
 
 // B2 of a small cell about its centre of mass e (offsets from particle ref),
-// summed directly so that no M|e|^2 cancels against the second moment.
-__device__ __forceinline__ float mom_b2_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-                                            uint32_t f, uint32_t n, uint32_t ref, float e0, float e1, float e2,
-                                            int lane)
+// summed directly so that no M|e|^2 cancels against the second moment, and
+// b_max, the largest distance of its particles to e.
+__device__ __forceinline__ void mom_b2_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo, uint32_t f,
+                                           uint32_t n, uint32_t ref, float e0, float e1, float e2, int lane, float &B2,
+                                           float &bmax)
 {
     const float4 hr = phi[ref], lr = plo[ref];
-    float q = 0.0f;
+    float q = 0.0f, d2max = 0.0f;
     for (uint32_t i = f + lane; i < f + n; i += 32) {
         const float4 h = phi[i], l = plo[i];
         const float d0 = ((h.x - hr.x) + (l.x - lr.x)) - e0, d1 = ((h.y - hr.y) + (l.y - lr.y)) - e1,
                     d2 = ((h.z - hr.z) + (l.z - lr.z)) - e2;
-        q = fmaf(h.w, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), q);
+        const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+        q = fmaf(h.w, r2, q);
+        d2max = fmaxf(d2max, r2);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-    return q;
+    for (int o = 16; o > 0; o >>= 1) {
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+        d2max = fmaxf(d2max, __shfl_xor_sync(0xffffffffu, d2max, o));
+    }
+    B2 = q;
+    bmax = sqrtf(d2max);
 }
 
 __device__ __forceinline__ MomSums mom_range(const MomArgs &a, uint32_t f, uint32_t n, double o0, double o1, double o2,
@@ -798,7 +812,125 @@ __device__ __forceinline__ void mom_store(const MomArgs &a, uint32_t c, const Mo
     store_com(a, c, r.M, c0, c1, c2, B2);
 }
 
-// every cell: small ones finished here, large ones get their chunk items
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// A larger cell from its (at most 8) children, one per lane, in a fixed order.
+// FP64 form in FP64. FP32 form in FP32 on offsets from the first child's
+// hi/lo centre of mass (hi differences exact), stored like a small cell's.
+template <bool F64>
+__device__ void mom_combine(const MomArgs &a, uint32_t c, int lane)
+{
+    const uint32_t ch0 = a.nchild[c], k = a.nnch[c];
+    const uint32_t f = a.nfirst[c];
+    const SysBox &b = a.box[a.psys[f]];
+    const bool on = (uint32_t)lane < k;
+    if (F64) {
+        double M = 0.0, x = 0.0, y = 0.0, z = 0.0, B2 = 0.0;
+        if (on) {
+            const uint32_t j = ch0 + lane;
+            M = __ldcg(a.M + j);
+            x = __ldcg(a.cx + j);
+            y = __ldcg(a.cy + j);
+            z = __ldcg(a.cz + j);
+            B2 = __ldcg(a.B2 + j);
+        }
+        const double rx = __shfl_sync(0xffffffffu, x, 0), ry = __shfl_sync(0xffffffffu, y, 0),
+                     rz = __shfl_sync(0xffffffffu, z, 0);
+        const double dx = x - rx, dy = y - ry, dz = z - rz;
+        const double Mt = warp_sum_d(M);
+        double c0, c1, c2, B2t = 0.0;
+        if (Mt > 0.0) {
+            const double ex = warp_sum_d(M * dx) / Mt, ey = warp_sum_d(M * dy) / Mt, ez = warp_sum_d(M * dz) / Mt;
+            c0 = rx + ex;
+            c1 = ry + ey;
+            c2 = rz + ez;
+            const double qx = dx - ex, qy = dy - ey, qz = dz - ez;
+            B2t = warp_sum_d(on ? B2 + M * (qx * qx + qy * qy + qz * qz) : 0.0);
+        } else {   // massless cell: its geometric centre
+            double o[3], sd;
+            cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
+            c0 = o[0] + 0.5 * sd;
+            c1 = o[1] + 0.5 * sd;
+            c2 = o[2] + 0.5 * sd;
+        }
+        if (lane == 0) store_com(a, c, Mt, c0, c1, c2, B2t);
+    } else {
+        float4 A = make_float4(0.0f, 0.0f, 0.0f, 0.0f), B = A;
+        if (on) {
+            A = __ldcg(a.nA + ch0 + lane);
+            B = __ldcg(a.nB + ch0 + lane);
+        }
+        const float hx = __shfl_sync(0xffffffffu, A.x, 0), hy = __shfl_sync(0xffffffffu, A.y, 0),
+                    hz = __shfl_sync(0xffffffffu, A.z, 0);
+        const float lx = __shfl_sync(0xffffffffu, B.x, 0), ly = __shfl_sync(0xffffffffu, B.y, 0),
+                    lz = __shfl_sync(0xffffffffu, B.z, 0);
+        const float M = A.w, dx = (A.x - hx) + (B.x - lx), dy = (A.y - hy) + (B.y - ly), dz = (A.z - hz) + (B.z - lz);
+        float Mt = M, sx = M * dx, sy = M * dy, sz = M * dz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        float e0, e1, e2, B2t = 0.0f;
+        if (Mt > 0.0f) {
+            e0 = sx / Mt;
+            e1 = sy / Mt;
+            e2 = sz / Mt;
+            const float qx = dx - e0, qy = dy - e1, qz = dz - e2;
+            B2t = on ? fmaf(M, qx * qx + qy * qy + qz * qz, B.w) : 0.0f;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) B2t += __shfl_xor_sync(0xffffffffu, B2t, o);
+        } else {   // massless cell: its geometric centre, relative to the first child's centre
+            double o[3], sd;
+            cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
+            e0 = (float)((o[0] + 0.5 * sd - b.lo[0]) - ((double)hx + (double)lx));
+            e1 = (float)((o[1] + 0.5 * sd - b.lo[1]) - ((double)hy + (double)ly));
+            e2 = (float)((o[2] + 0.5 * sd - b.lo[2]) - ((double)hz + (double)lz));
+        }
+        if (lane == 0) {
+            const float t0 = lx + e0, t1 = ly + e1, t2 = lz + e2;
+            const float g0 = rintf(t0 * b.inv_uf) * b.uf, g1 = rintf(t1 * b.inv_uf) * b.uf,
+                        g2 = rintf(t2 * b.inv_uf) * b.uf;
+            a.nA[c] = make_float4(hx + g0, hy + g1, hz + g2, Mt);
+            a.nB[c] = make_float4(t0 - g0, t1 - g1, t2 - g2, B2t);
+        }
+    }
+}
+
+// After cell c is final: if its parent is a larger cell and c is the last of
+// its children to finish, combine the parent, and so on upwards.
+template <bool F64>
+__device__ void mom_climb(const MomArgs &a, uint32_t c, int lane)
+{
+    for (;;) {
+        const uint32_t p = a.nparent[c];
+        if (p == NONE || a.ncount[p] <= MOM_CH) return;
+        __syncwarp();
+        unsigned int old = 0;
+        if (lane == 0) {   // release: c's moments (stored by this lane) before the count; acquire: the others' after
+            cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(a.done[p]);
+            old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old + 1u != a.nnch[p]) return;
+        __syncwarp();
+        mom_combine<F64>(a, p, lane);
+        c = p;
+    }
+}
+
+constexpr uint32_t BM_CH = 256;
+
+// every cell of at most MOM_CH particles, and every leaf (a leaf holds more
+// only when its particles share one level-21 cell): moments and b_max from its
+// particles, then the climb; larger cells get their b_max chunk items
 template <bool F64>
 __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long *nitems, uint32_t *bigbase,
                                                    uint32_t *items, uint32_t cap_items, Status *st, int where)
@@ -809,23 +941,37 @@ __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
         const uint32_t f = a.nfirst[c], n = a.ncount[c];
-        const bool leaf = a.nnch[c] == 0;
-        if (n <= MOM_CH) {
-            if (leaf)
-                for (uint32_t i = f + lane; i < f + n; i += 32) a.leafof[i] = c;
+        if (n <= MOM_CH || a.nnch[c] == 0) {
             if (F64) {
                 const double o0 = a.x[f], o1 = a.y[f], o2 = a.z[f];
                 const MomSums r = mom_range(a, f, n, o0, o1, o2, lane);
                 if (lane == 0) mom_store(a, c, r, o0, o1, o2);
+                __syncwarp();
+                const double c0 = __shfl_sync(0xffffffffu, lane == 0 ? a.cx[c] : 0.0, 0);
+                const double c1 = __shfl_sync(0xffffffffu, lane == 0 ? a.cy[c] : 0.0, 0);
+                const double c2 = __shfl_sync(0xffffffffu, lane == 0 ? a.cz[c] : 0.0, 0);
+                double dm = 0.0;
+                for (uint32_t i = f + lane; i < f + n; i += 32) {
+                    const double d0 = a.x[i] - c0, d1 = a.y[i] - c1, d2 = a.z[i] - c2;
+                    dm = fmax(dm, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+                if (lane == 0) a.bmax64[c] = (unsigned long long)__double_as_longlong(dm);
             } else {
                 const MomSumsF r = mom_range_f32(a.phi, a.plo, f, n, f, lane);
                 const float iM = r.M > 0.0f ? 1.0f / r.M : 0.0f;
                 const float e0 = r.sx * iM, e1 = r.sy * iM, e2 = r.sz * iM;
-                const float B2 = mom_b2_f32(a.phi, a.plo, f, n, f, e0, e1, e2, lane);
-                if (lane == 0) mom_store_f32(a, c, f, r.M, e0, e1, e2, B2);
+                float B2, bm;
+                mom_b2_f32(a.phi, a.plo, f, n, f, e0, e1, e2, lane, B2, bm);
+                if (lane == 0) {
+                    mom_store_f32(a, c, f, r.M, e0, e1, e2, B2);
+                    a.bmax32[c] = __float_as_uint(bm);
+                }
             }
+            mom_climb<F64>(a, c, lane);
         } else if (lane == 0) {
-            const uint32_t nch = (n + MOM_CH - 1) / MOM_CH;
+            const uint32_t nch = (n + BM_CH - 1) / BM_CH;
             const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
             if (base + nch > cap_items) {
                 fail(st, HYBRID_ECAPACITY, where);
@@ -837,11 +983,11 @@ __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long
     }
 }
 
-// chunk sums of large cells
+// b_max of the larger cells: one warp per chunk of BM_CH particles, one atomic
+// max per chunk (non-negative floats order as their bit patterns)
 template <bool F64>
-__global__ void __launch_bounds__(256) k_mom_chunks(MomArgs a, const unsigned long long *nitems,
-                                                    const uint32_t *bigbase, const uint32_t *items,
-                                                    MomSums *partial, const Status *st)
+__global__ void __launch_bounds__(256) k_bmax_big(MomArgs a, const unsigned long long *nitems,
+                                                  const uint32_t *bigbase, const uint32_t *items, const Status *st)
 {
     if (st->code) return;
     const uint32_t T = (uint32_t)*nitems;
@@ -851,141 +997,30 @@ __global__ void __launch_bounds__(256) k_mom_chunks(MomArgs a, const unsigned lo
         const uint32_t c = items[w];
         const uint32_t k = w - bigbase[c];
         const uint32_t f = a.nfirst[c], n = a.ncount[c];
-        const uint32_t f0 = f + k * MOM_CH, n0 = min(MOM_CH, f + n - f0);
-        if (a.nnch[c] == 0)
-            for (uint32_t i = f0 + lane; i < f0 + n0; i += 32) a.leafof[i] = c;
-        MomSums r;
+        const uint32_t f0 = f + k * BM_CH, n0 = min(BM_CH, f + n - f0);
         if (F64) {
-            r = mom_range(a, f0, n0, a.x[f], a.y[f], a.z[f], lane);
+            const double c0 = a.cx[c], c1 = a.cy[c], c2 = a.cz[c];
+            double dm = 0.0;
+            for (uint32_t i = f0 + lane; i < f0 + n0; i += 32) {
+                const double d0 = a.x[i] - c0, d1 = a.y[i] - c1, d2 = a.z[i] - c2;
+                dm = fmax(dm, sqrt(d0 * d0 + d1 * d1 + d2 * d2));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+            if (lane == 0) atomicMax(a.bmax64 + c, (unsigned long long)__double_as_longlong(dm));
         } else {
-            const MomSumsF q = mom_range_f32(a.phi, a.plo, f0, n0, f, lane);
-            r.M = q.M;
-            r.sx = q.sx;
-            r.sy = q.sy;
-            r.sz = q.sz;
-            r.Q = q.Q;
-        }
-        if (lane == 0) partial[w] = r;
-    }
-}
-
-// large cells: chunk sums added in chunk order
-template <bool F64>
-__global__ void __launch_bounds__(256) k_mom_big(MomArgs a, const uint32_t *bigbase, const MomSums *partial,
-                                                 const Status *st)
-{
-    if (st->code) return;
-    const uint32_t total = a.lvl[LEVELS + 1];
-    const int lane = threadIdx.x & 31;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
-        const uint32_t f = a.nfirst[c], n = a.ncount[c];
-        if (n <= MOM_CH) continue;
-        const uint32_t nch = (n + MOM_CH - 1) / MOM_CH, b0 = bigbase[c];
-        MomSums r = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (uint32_t k = lane; k < nch; k += 32) {
-            const MomSums q = partial[b0 + k];
-            r.M += q.M;
-            r.sx += q.sx;
-            r.sy += q.sy;
-            r.sz += q.sz;
-            r.Q += q.Q;
-        }
+            const float4 A = a.nA[c], B = a.nB[c];
+            float dm = 0.0f;
+            for (uint32_t i = f0 + lane; i < f0 + n0; i += 32) {
+                const float4 h = a.phi[i], l = a.plo[i];
+                const float d0 = (h.x - A.x) + (l.x - B.x);
+                const float d1 = (h.y - A.y) + (l.y - B.y);
+                const float d2 = (h.z - A.z) + (l.z - B.z);
+                dm = fmaxf(dm, d0 * d0 + d1 * d1 + d2 * d2);
+            }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            r.M += __shfl_xor_sync(0xffffffffu, r.M, o);
-            r.sx += __shfl_xor_sync(0xffffffffu, r.sx, o);
-            r.sy += __shfl_xor_sync(0xffffffffu, r.sy, o);
-            r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
-            r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
-        }
-        if (lane == 0) {
-            if (F64) mom_store(a, c, r, a.x[f], a.y[f], a.z[f]);
-            else {
-                // few large cells: finish in FP64 (parallel-axis form), store in FP32
-                double e0 = 0.0, e1 = 0.0, e2 = 0.0, B2 = 0.0;
-                if (r.M > 0.0) {
-                    e0 = r.sx / r.M;
-                    e1 = r.sy / r.M;
-                    e2 = r.sz / r.M;
-                    B2 = fmax(r.Q - r.M * (e0 * e0 + e1 * e1 + e2 * e2), 0.0);
-                }
-                mom_store_f32(a, c, f, (float)r.M, (float)e0, (float)e1, (float)e2, (float)B2);
-            }
-        }
-    }
-}
-
-// b_max = max over members of |x_i - com|: every particle visits its
-// ancestors level by level; lanes of a warp that share a node reduce with a
-// segmented max (sorted particles: a node's lanes are contiguous), then one
-// atomic max per run. F64: FP64 distance; else FP32 from the hi/lo copies.
-template <bool F64>
-__global__ void __launch_bounds__(256) k_bmax(int64_t N, const uint32_t *__restrict__ leafof,
-                                              const uint32_t *__restrict__ nparent,
-                                              const uint32_t *__restrict__ nlevel, const double *__restrict__ x,
-                                              const double *__restrict__ y, const double *__restrict__ z,
-                                              const double *__restrict__ cx, const double *__restrict__ cy,
-                                              const double *__restrict__ cz, const float4 *__restrict__ phi,
-                                              const float4 *__restrict__ plo, const float4 *__restrict__ nA,
-                                              const float4 *__restrict__ nB, unsigned long long *bmax,
-                                              unsigned int *bmax32, const Status *st)
-{
-    using T = typename std::conditional<F64, double, float>::type;
-    if (st->code) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t nwarp_total = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t wb = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; wb * 32 < N; wb += nwarp_total) {
-        const int64_t i = wb * 32 + lane;
-        const bool ok = i < N;
-        uint32_t c = ok ? leafof[i] : NONE;
-        int lev = ok ? (int)nlevel[c] : -1;
-        int maxlev = lev;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) maxlev = max(maxlev, __shfl_xor_sync(0xffffffffu, maxlev, o));
-        double px = 0, py = 0, pz = 0;
-        float4 ph = make_float4(0, 0, 0, 0), pl = ph;
-        if (ok) {
-            if (F64) {
-                px = x[i];
-                py = y[i];
-                pz = z[i];
-            } else {
-                ph = phi[i];
-                pl = plo[i];
-            }
-        }
-        for (int L = maxlev; L >= 0; --L) {
-            const bool act = (lev == L);
-            T dist = T(0);
-            if (act) {
-                if (F64) {
-                    const double d0 = px - cx[c], d1 = py - cy[c], d2 = pz - cz[c];
-                    dist = (T)sqrt(d0 * d0 + d1 * d1 + d2 * d2);
-                } else {
-                    const float4 A = nA[c], B = nB[c];
-                    const float d0 = (ph.x - A.x) + (pl.x - B.x);
-                    const float d1 = (ph.y - A.y) + (pl.y - B.y);
-                    const float d2 = (ph.z - A.z) + (pl.z - B.z);
-                    dist = (T)sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
-                }
-            }
-            const uint32_t keyv = act ? c : NONE;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const T du = __shfl_up_sync(0xffffffffu, dist, o);
-                const uint32_t ku = __shfl_up_sync(0xffffffffu, keyv, o);
-                if (lane >= o && ku == keyv) dist = dist > du ? dist : du;
-            }
-            const uint32_t kd = __shfl_down_sync(0xffffffffu, keyv, 1);
-            if (act && (lane == 31 || kd != keyv)) {
-                if (F64) atomicMax(&bmax[c], (unsigned long long)__double_as_longlong((double)dist));
-                else atomicMax(&bmax32[c], __float_as_uint((float)dist));   // non-negative: bit order = value order
-            }
-            if (act) {
-                c = nparent[c];
-                lev = L - 1;
-            }
+            for (int o = 16; o > 0; o >>= 1) dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, o));
+            if (lane == 0) atomicMax(a.bmax32 + c, __float_as_uint(sqrtf(dm)));
         }
     }
 }
@@ -1340,38 +1375,23 @@ void launch_moments(hybrid_ctx *c)
     a.nA = (float4 *)c->nA.p;
     a.nB = (float4 *)c->nB.p;
     a.done = (uint32_t *)c->ndone.p;
-    a.leafof = (uint32_t *)c->leafof.p;
-    unsigned long long *nitems = (unsigned long long *)c->counter.p + 9;
-    cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), c->st);
-    const int gridw = grid_for(c, c->capNodes * 32, 256, 16);
+    a.bmax64 = (unsigned long long *)c->nbmax.p;
+    a.bmax32 = (unsigned int *)c->nbmax32.p;
     a.phi = (const float4 *)c->phi.p;
     a.plo = (const float4 *)c->plo.p;
+    unsigned long long *nitems = (unsigned long long *)c->counter.p + 9;
+    cudaMemsetAsync(nitems, 0, sizeof(unsigned long long), c->st);
+    cudaMemsetAsync(c->ndone.p, 0, (size_t)c->capNodes * sizeof(uint32_t), c->st);
+    const int gridw = grid_for(c, c->capNodes * 32, 256, 16);
+    uint32_t *bigbase = (uint32_t *)c->nbig.p, *items = (uint32_t *)c->mitems.p;
     if (c->p.precision == 0) {
-        k_mom_small<true><<<gridw, 256, 0, c->st>>>(a, nitems, (uint32_t *)c->nbig.p, (uint32_t *)c->mitems.p,
-                                                    (uint32_t)c->capItems, st, c->op);
-        k_mom_chunks<true><<<gridw, 256, 0, c->st>>>(a, nitems, (const uint32_t *)c->nbig.p,
-                                                     (const uint32_t *)c->mitems.p, (MomSums *)c->mpart.p, st);
+        k_mom_small<true><<<gridw, 256, 0, c->st>>>(a, nitems, bigbase, items, (uint32_t)c->capItems, st, c->op);
+        k_bmax_big<true><<<gridw, 256, 0, c->st>>>(a, nitems, bigbase, items, st);
     } else {
-        k_mom_small<false><<<gridw, 256, 0, c->st>>>(a, nitems, (uint32_t *)c->nbig.p, (uint32_t *)c->mitems.p,
-                                                     (uint32_t)c->capItems, st, c->op);
-        k_mom_chunks<false><<<gridw, 256, 0, c->st>>>(a, nitems, (const uint32_t *)c->nbig.p,
-                                                      (const uint32_t *)c->mitems.p, (MomSums *)c->mpart.p, st);
+        k_mom_small<false><<<gridw, 256, 0, c->st>>>(a, nitems, bigbase, items, (uint32_t)c->capItems, st, c->op);
+        k_bmax_big<false><<<gridw, 256, 0, c->st>>>(a, nitems, bigbase, items, st);
     }
-    if (c->p.precision == 0)
-        k_mom_big<true><<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
-    else
-        k_mom_big<false><<<gridw, 256, 0, c->st>>>(a, (const uint32_t *)c->nbig.p, (const MomSums *)c->mpart.p, st);
     c->launches += 2;
-    const int gridp = grid_for(c, c->N, 256, 8);
-    if (c->p.precision == 0)
-        k_bmax<true><<<gridp, 256, 0, c->st>>>(
-            c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, a.x, a.y,
-            a.z, a.cx, a.cy, a.cz, nullptr, nullptr, nullptr, nullptr, (unsigned long long *)c->nbmax.p, nullptr, st);
-    else
-        k_bmax<false><<<gridp, 256, 0, c->st>>>(
-            c->N, (const uint32_t *)c->leafof.p, (const uint32_t *)c->nparent.p, (const uint32_t *)c->nlevel.p, nullptr,
-            nullptr, nullptr, nullptr, nullptr, nullptr, (const float4 *)c->phi.p, (const float4 *)c->plo.p, a.nA, a.nB,
-            nullptr, (unsigned int *)c->nbmax32.p, st);
     FinArgs f;
     f.lvl = a.lvl;
     f.nfirst = a.nfirst;

@@ -297,7 +297,6 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
     Status *st = a.st;
     if (st->code) return;
     const int lane = threadIdx.x & 31;
-    const unsigned ltmask = (1u << lane) - 1u;
     const int64_t ng = *a.ngroups;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     uint32_t *stk = a.stack + gw * a.cap_stack;
