@@ -161,6 +161,7 @@ constexpr int PER = TILE / 32;
 // packed two-sink arithmetic, in tile[0, 2 PADT): entries from nt up to
 // PADT = TILE + 32 are zero-mass sources.
 constexpr int PADT = TILE + 32;
+static_assert(2 * PADT >= 3 * TILE, "the near filter keeps three float4 rows of TILE entries");
 template <int NST>
 struct WarpStage {
     float4 tile[2 * PADT];
@@ -213,9 +214,23 @@ struct ItemSrc {
 
 // Runs the staging pipeline over the item's entries and calls
 // body(stage, nt) once per tile, after the tile has been rebased into S.tile.
-template <bool PACKED, int NST, typename Body>
+// Box of a warp's sinks (group-relative FP32) for the near filter.
+struct SinkBox {
+    float lo[3], hi[3], R2sq;
+};
+
+// Staging modes: FAR_PACKED writes every source twice over for the packed far
+// sweep and calls body(stage, nt). NEAR_FILTER keeps a source for the near
+// body only when its distance to the sinks' box is below R2 (computed like the
+// pair distance, so no pair with r < R2 is dropped): kept sources go to
+// tile[0, n_in) with their rebased hi part at tile[TILE + j] and raw lo part at
+// tile[2 TILE + j]; the others (K = 0 for every sink) to tile[TILE - n_out,
+// TILE); then body(n_in, n_out).
+enum { FAR_PACKED = 0, NEAR_FILTER = 1 };
+
+template <int SMODE, int NST, typename Body>
 __device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, WarpStage<NST> &S, int lane,
-                                         float crx, float cry, float crz, Body &&body)
+                                         float crx, float cry, float crz, const SinkBox &sb, Body &&body)
 {
     static_assert(NST >= 2 && NST <= 4, "staging depth");
     const uint32_t ne = src.e1 - src.e0;
@@ -236,23 +251,58 @@ __device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, 
         cp_wait<NST - 1>();                       // this lane's copies of tile t have landed
         const int st = t % NST;
         const int nt = (int)min((uint32_t)TILE, ne - (uint32_t)(t * TILE));
+        if (SMODE == FAR_PACKED) {
 #pragma unroll
-        for (int u = 0; u < PER; ++u) {   // entries past nt become zero-mass sources
-            const int el = u * 32 + lane;
-            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (el < nt) {
-                const float4 h = S.rh[st][el], l = S.rl[st][el];
-                v = make_float4((h.x - crx) + l.x, (h.y - cry) + l.y, (h.z - crz) + l.z, h.w);
-            }
-            if (PACKED) {
+            for (int u = 0; u < PER; ++u) {   // entries past nt become zero-mass sources
+                const int el = u * 32 + lane;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (el < nt) {
+                    const float4 h = S.rh[st][el], l = S.rl[st][el];
+                    v = make_float4((h.x - crx) + l.x, (h.y - cry) + l.y, (h.z - crz) + l.z, h.w);
+                }
                 S.tile[2 * el] = make_float4(v.x, v.x, v.y, v.y);
                 S.tile[2 * el + 1] = make_float4(v.z, v.z, v.w, v.w);
-            } else {
-                S.tile[el] = v;
             }
+            __syncwarp();
+            body(st, nt);
+        } else {
+            float4 v[PER], vh[PER], vl[PER];
+            bool keep[PER], out[PER];
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int el = u * 32 + lane;
+                keep[u] = out[u] = false;
+                if (el < nt) {
+                    const float4 h = S.rh[st][el], l = S.rl[st][el];
+                    vh[u] = make_float4(h.x - crx, h.y - cry, h.z - crz, 0.0f);
+                    vl[u] = l;
+                    v[u] = make_float4(vh[u].x + l.x, vh[u].y + l.y, vh[u].z + l.z, h.w);
+                    const float gx = fmaxf(fmaxf(sb.lo[0] - v[u].x, v[u].x - sb.hi[0]), 0.0f);
+                    const float gy = fmaxf(fmaxf(sb.lo[1] - v[u].y, v[u].y - sb.hi[1]), 0.0f);
+                    const float gz = fmaxf(fmaxf(sb.lo[2] - v[u].z, v[u].z - sb.hi[2]), 0.0f);
+                    keep[u] = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) < sb.R2sq;
+                    out[u] = !keep[u];
+                }
+            }
+            const unsigned ltm = (1u << lane) - 1u;
+            const unsigned k0 = __ballot_sync(0xffffffffu, keep[0]), k1 = __ballot_sync(0xffffffffu, keep[1]);
+            const unsigned o0 = __ballot_sync(0xffffffffu, out[0]), o1 = __ballot_sync(0xffffffffu, out[1]);
+            const int n_in = __popc(k0) + __popc(k1), n_out = __popc(o0) + __popc(o1);
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {   // order kept within each part
+                if (keep[u]) {
+                    const int j = u == 0 ? __popc(k0 & ltm) : __popc(k0) + __popc(k1 & ltm);
+                    S.tile[j] = v[u];
+                    S.tile[TILE + j] = vh[u];
+                    S.tile[2 * TILE + j] = vl[u];
+                } else if (out[u]) {
+                    const int j = u == 0 ? __popc(o0 & ltm) : __popc(o0) + __popc(o1 & ltm);
+                    S.tile[TILE - n_out + j] = v[u];
+                }
+            }
+            __syncwarp();
+            body(n_in, n_out);
         }
-        __syncwarp();
-        body(st, nt);
         __syncwarp();
     }
 }
@@ -399,9 +449,9 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                 int si = r0 + kk * lpc + slot;
                 si = si < n ? si : n - 1;
                 const float4 h = a.phi[first + si], l = a.plo[first + si];
-                shx[kk] = h.x;
-                shy[kk] = h.y;
-                shz[kk] = h.z;
+                shx[kk] = h.x - crx;   // rebased hi (exact): differences with the staged sources' are exact
+                shy[kk] = h.y - cry;
+                shz[kk] = h.z - crz;
                 slx[kk] = l.x;
                 sly[kk] = l.y;
                 slz[kk] = l.z;
@@ -424,11 +474,11 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                 }
                 const uint64_t E2 = pk2(H.eps2, H.eps2);
                 if (H.eps2 > 0.0f)
-                    pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
+                    pipeline<FAR_PACKED>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
                         far_tile<KP, false, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
                     });
                 else   // eps = 0 without a hard part: a sink meets itself in its far particles
-                    pipeline<true>(a, src, S, lane, crx, cry, crz, [&](int, int nt) {
+                    pipeline<FAR_PACKED>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
                         far_tile<KP, true, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
                     });
 #pragma unroll
@@ -445,9 +495,39 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                     if (2 * p + 1 < KS) az[2 * p + 1] = t1;
                 }
             } else {
-                pipeline<false>(a, src, S, lane, crx, cry, crz, [&](int st, int nt) {
+                // the box of this round's sinks: sources farther than R2 from it have K = 0 for every sink
+                SinkBox sb;
+                sb.R2sq = H.R2sq;
+                {
+                    float lo0 = sx[0], lo1 = sy[0], lo2 = sz[0], hi0 = sx[0], hi1 = sy[0], hi2 = sz[0];
+#pragma unroll
+                    for (int k = 1; k < KS; ++k) {
+                        lo0 = fminf(lo0, sx[k]);
+                        lo1 = fminf(lo1, sy[k]);
+                        lo2 = fminf(lo2, sz[k]);
+                        hi0 = fmaxf(hi0, sx[k]);
+                        hi1 = fmaxf(hi1, sy[k]);
+                        hi2 = fmaxf(hi2, sz[k]);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        lo0 = fminf(lo0, __shfl_xor_sync(0xffffffffu, lo0, o));
+                        lo1 = fminf(lo1, __shfl_xor_sync(0xffffffffu, lo1, o));
+                        lo2 = fminf(lo2, __shfl_xor_sync(0xffffffffu, lo2, o));
+                        hi0 = fmaxf(hi0, __shfl_xor_sync(0xffffffffu, hi0, o));
+                        hi1 = fmaxf(hi1, __shfl_xor_sync(0xffffffffu, hi1, o));
+                        hi2 = fmaxf(hi2, __shfl_xor_sync(0xffffffffu, hi2, o));
+                    }
+                    sb.lo[0] = lo0;
+                    sb.lo[1] = lo1;
+                    sb.lo[2] = lo2;
+                    sb.hi[0] = hi0;
+                    sb.hi[1] = hi1;
+                    sb.hi[2] = hi2;
+                }
+                pipeline<NEAR_FILTER>(a, src, S, lane, crx, cry, crz, sb, [&](int n_in, int n_out) {
                     if (!active) return;
-                    for (int j = copy; j < nt; j += copies) {
+                    for (int j = copy; j < n_in; j += copies) {   // sources within R2 of the box
                         const float4 q = S.tile[j];
                         float dx[KS], dy[KS], dz[KS], r2u[KS];
                         bool any_in = false;
@@ -461,8 +541,8 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                         }
                         float4 hh = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ll = hh;
                         if (any_in) {
-                            hh = S.rh[st][j];
-                            ll = S.rl[st][j];
+                            hh = S.tile[TILE + j];
+                            ll = S.tile[2 * TILE + j];
                         }
 #pragma unroll
                         for (int k = 0; k < KS; ++k)
@@ -470,6 +550,12 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                                                     slx[k], sly[k], slz[k], H, ax[k], ay[k], az[k], bx[k], by[k],
                                                     bz[k]);
                     }
+                    if (SOFT)   // the rest: K = 0 for every sink, weight 1 on the soft force
+                        for (int j = TILE - n_out + copy; j < TILE; j += copies) {
+                            const float4 q = S.tile[j];
+#pragma unroll
+                            for (int k = 0; k < KS; ++k) body_far<false>(q, sx[k], sy[k], sz[k], H.eps2, ax[k], ay[k], az[k]);
+                        }
                 });
             }
             if (SOFT) reduce_copies<KS>(lane, copy, copies, lpc, ax, ay, az);
