@@ -64,6 +64,7 @@ struct WalkArgs {
 };
 
 constexpr uint32_t WALK_REGION = 2048;
+constexpr int WALK_SSTK = 1024;   // entries of a warp's stack kept in shared memory (one walk iteration pushes <= 256)
 
 __device__ __forceinline__ void fail(Status *st, int code, int where)
 {
@@ -299,7 +300,9 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
     const int lane = threadIdx.x & 31;
     const int64_t ng = *a.ngroups;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    uint32_t *stk = a.stack + gw * a.cap_stack;
+    uint32_t *stk = a.stack + gw * a.cap_stack;   // overflow part of the stack (older entries)
+    __shared__ uint32_t sstk_all[WALK_THREADS / 32][WALK_SSTK];
+    uint32_t *sstk = sstk_all[threadIdx.x >> 5];    // top part of the stack
     const bool want_soft = a.mode & 1, want_hard = (a.mode >> 1) & 1;
     uint64_t my_cur = 0, my_end = 0, my_start = 0, my_len = 0;   // kind = lane (lanes 0..2)
     bool fail_list = false, fail_items = false, overflow = false;
@@ -319,9 +322,10 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
         my_start = my_cur;
         my_len = 0;
         uint32_t early_far = 0, early_near = 0;   // items already emitted for this group
-        int64_t sp = 0;
+        int sp = 0;        // entries in the shared-memory part
+        int64_t gp = 0;    // entries in the global part
         if (want_soft || wh0) {
-            if (lane == 0) stk[0] = a.sysroot[s] | ((uint32_t)want_soft << 30) | ((uint32_t)wh0 << 31);
+            if (lane == 0) sstk[0] = a.sysroot[s] | ((uint32_t)want_soft << 30) | ((uint32_t)wh0 << 31);
             sp = 1;
         }
         __syncwarp();
@@ -355,10 +359,17 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
             }
             return base;
         };
-        while (sp > 0) {
-            const int take = (int)(sp < 32 ? sp : 32);
+        while (sp > 0 || gp > 0) {
+            if (sp == 0) {   // refill the shared part from the top of the global part
+                const int m = (int)(gp < WALK_SSTK / 2 ? gp : WALK_SSTK / 2);
+                for (int j = lane; j < m; j += 32) sstk[j] = stk[gp - m + j];
+                gp -= m;
+                sp = m;
+                __syncwarp();
+            }
+            const int take = sp < 32 ? sp : 32;
             uint32_t e = 0;
-            if (lane < take) e = stk[sp - take + lane];
+            if (lane < take) e = sstk[sp - take + lane];
             sp -= take;
             __syncwarp();
             const bool valid = lane < take;
@@ -410,15 +421,21 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
                 uint32_t tot;
                 const uint32_t k = open ? T.y : 0u;
                 const uint32_t ex = warp_excl_scan(k, tot);
-                if (sp + (int64_t)tot > a.cap_stack) {
-                    overflow = true;
-                    break;
+                if (sp + (int)tot > WALK_SSTK) {   // move the shared part under the global part
+                    if (gp + sp > a.cap_stack) {
+                        overflow = true;
+                        break;
+                    }
+                    for (int j = lane; j < sp; j += 32) stk[gp + j] = sstk[j];
+                    gp += sp;
+                    sp = 0;
+                    __syncwarp();
                 }
                 if (open) {
                     const uint32_t fl = ((uint32_t)open_s << 30) | ((uint32_t)open_h << 31);
-                    for (uint32_t j = 0; j < k; ++j) stk[sp + ex + j] = (T.x + j) | fl;
+                    for (uint32_t j = 0; j < k; ++j) sstk[sp + ex + j] = (T.x + j) | fl;
                 }
-                sp += tot;
+                sp += (int)tot;
             }
             __syncwarp();
         }
