@@ -410,6 +410,8 @@ def run_c3(args):
     stream = torch.cuda.current_stream()
     ctx = hybrid.Context(P, stream)
     s = hybrid.System(st, precision=1, ids=False)
+    chosen, _ = ctx.hybrid_autotune(s, [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0),
+                                         (256, 64, 2), (256, 32, 0)])
     ctx.hybrid_step(s, 0)
     for _ in range(args.warmup):
         ctx.hybrid_step(s, 1)
@@ -451,7 +453,8 @@ def run_c3(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "Hernquist sphere N=%d seed 2, a=1, r<=100, eps=1/512, theta=0.4, R1=3eps, "
                                "R2=6eps, dt_s=1/128, n_hard=8; FP32 pairs, FP64 state" % n,
-                   "N": n, "l2": "inputs larger than L2", "ic_seconds": t_ic},
+                   "N": n, "l2": "inputs larger than L2", "ic_seconds": t_ic,
+                   "autotuned": {"n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]}},
         "interactions_per_s": (inter_far + P.n_hard * inter_near) / t,
         "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
         "hard_interactions_per_substep": inter_near / args.steps,

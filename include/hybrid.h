@@ -148,7 +148,7 @@ hybrid_status hybrid_step_batched(hybrid_ctx *ctx, hybrid_system *sys, int n_sys
 
 /* Autotuner (an implementation choice, not part of the method): for each
  * candidate (n_crit, threads_per_group, tile_depth) -- cand holds n_cand
- * triples; cand = NULL, n_cand = 0 uses a built-in list of 14 -- times one
+ * triples; cand = NULL, n_cand = 0 uses a built-in list of 18 -- times one
  * soft evaluation (tree build, walk, far and near pairs) and one hard
  * evaluation (build, hard walk, near pairs) of the given systems with CUDA
  * events after one untimed run, and estimates the time of a soft step as

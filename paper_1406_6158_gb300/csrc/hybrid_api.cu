@@ -832,7 +832,8 @@ hybrid_status hybrid_autotune(hybrid_ctx *c, hybrid_system *sys, int n_sys, cons
 {
     static const int32_t defaults[][3] = {
         {16, 4, 0},  {16, 8, 0},  {32, 8, 0},  {32, 16, 0}, {64, 16, 0},  {64, 32, 0}, {128, 32, 0}, {128, 64, 0},
-        {32, 8, 2},  {32, 8, 4},  {64, 16, 2}, {64, 16, 4}, {128, 32, 2}, {128, 32, 4}};
+        {32, 8, 2},  {32, 8, 4},  {64, 16, 2}, {64, 16, 4}, {128, 32, 2}, {128, 32, 4}, {256, 64, 0},
+        {256, 64, 2}, {128, 16, 0}, {256, 32, 0}};
     if (!c || !sys || n_sys < 1 || n_cand < 0 || (n_cand > 0 && !cand)) return HYBRID_EINVAL;
     const int32_t *cv = n_cand > 0 ? cand : &defaults[0][0];
     const int nc = n_cand > 0 ? n_cand : (int)(sizeof(defaults) / sizeof(defaults[0]));

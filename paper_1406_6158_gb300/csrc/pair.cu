@@ -734,19 +734,20 @@ void go_f32(hybrid_ctx *c, const PairArgs &a)
     else k_pair_f32<KS, NEAR, SOFT, HARD, 3><<<c->nsm * 16, PAIR_THREADS, 0, c->st>>>(a);
 }
 
-// Sinks per lane KS = ceil(n_crit / threads_per_group), from 1 to 4; the
-// default is 4 (one shared-memory read feeds 4 interactions; the far kernel
-// runs them as two packed sink pairs).
+// Sinks per lane KS = ceil(n_crit / threads_per_group): 1, 2, 4 or (far
+// kernel only) 8; the default is 4 (one shared-memory read feeds 4
+// interactions; the far kernel runs them as packed sink pairs).
 template <bool NEAR, bool SOFT, bool HARD>
 void go_ks(hybrid_ctx *c, const PairArgs &a)
 {
     int ks;
     if (c->p.threads_per_group > 0) ks = (c->p.n_crit + c->p.threads_per_group - 1) / c->p.threads_per_group;
     else ks = 4;
-    ks = ks <= 1 ? 1 : (ks <= 2 ? 2 : 4);
+    ks = ks <= 1 ? 1 : (ks <= 2 ? 2 : (ks <= 4 || NEAR ? 4 : 8));   // 8 sinks per lane: far kernel only
     if (ks == 1) go_f32<1, NEAR, SOFT, HARD>(c, a);
     else if (ks == 2) go_f32<2, NEAR, SOFT, HARD>(c, a);
-    else go_f32<4, NEAR, SOFT, HARD>(c, a);
+    else if (ks == 4) go_f32<4, NEAR, SOFT, HARD>(c, a);
+    else if constexpr (!NEAR) go_f32<8, NEAR, SOFT, HARD>(c, a);
 }
 
 // near = false: cells and far particles (soft); near = true: near particles

@@ -300,7 +300,7 @@ class Context:
         systems = [systems] if isinstance(systems, System) else list(systems)
         arr = (hybrid_system * len(systems))(*[s.c for s in systems])
         if candidates is None:
-            cand, nc, nout = None, 0, 14
+            cand, nc, nout = None, 0, 18
         else:
             flat = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32).reshape(-1, 3))
             cand, nc, nout = flat, len(flat), len(flat)
@@ -309,7 +309,8 @@ class Context:
         self._check("hybrid_autotune", self.L.hybrid_autotune(
             self.h, arr, len(systems), None if cand is None else cand.ctypes.data, nc, ms.ctypes.data, C.byref(best)))
         defaults = [(16, 4, 0), (16, 8, 0), (32, 8, 0), (32, 16, 0), (64, 16, 0), (64, 32, 0), (128, 32, 0),
-                    (128, 64, 0), (32, 8, 2), (32, 8, 4), (64, 16, 2), (64, 16, 4), (128, 32, 2), (128, 32, 4)]
+                    (128, 64, 0), (32, 8, 2), (32, 8, 4), (64, 16, 2), (64, 16, 4), (128, 32, 2), (128, 32, 4),
+                    (256, 64, 0), (256, 64, 2), (128, 16, 0), (256, 32, 0)]
         table = defaults if cand is None else [tuple(int(v) for v in row) for row in cand]
         chosen = table[best.value]
         self.params = dataclasses.replace(self.params, n_crit=chosen[0], threads_per_group=chosen[1],
