@@ -535,6 +535,7 @@ def main():
         chosen = tuple(int(v) for v in args.tune.split(","))
         ctx.hybrid_autotune(s, [chosen])
     ctx.hybrid_step(s, 0)                      # forces at the initial positions
+    e_start = sum(ctx.hybrid_energy(s))        # softened total energy by direct FP64 summation (device)
     for _ in range(args.warmup):
         ctx.hybrid_step(s, 1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -573,6 +574,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_steps = float(t.item())
     value = ws * w["n"] * args.steps / t_steps
+    e_end = sum(ctx.hybrid_energy(s))
+    energy = {"rel_drift": abs(e_end - e_start) / abs(e_start), "E_start": e_start, "E_end": e_end,
+              "soft_steps": args.warmup + args.steps, "time": (args.warmup + args.steps) * w["dt_soft"]}
 
     # ---- end to end through the C-ABI with host buffers ----
     e2e = None
@@ -638,6 +642,7 @@ def main():
             "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
             "hard_interactions_per_substep": inter_near / args.steps,
             "force_err_rms_vs_direct": ferr,
+            "energy": energy,
             "kernel_ms_per_step": {"far_pair": soft_ms / args.steps, "near_pair": hard_ms / args.steps,
                                    "walk": walk_ms / args.steps, "tree_build": tree_ms / args.steps,
                                    "kick_drift": integ_ms / args.steps,

@@ -218,6 +218,31 @@ def test_lists_and_forces(H, name, mk, kw, prec):
     assert abs(far + near - os_) <= 1e-3 * os_
 
 
+@pytest.mark.parametrize("n_crit,tpg,depth", [(64, 8, 0), (256, 32, 2), (32, 16, 4), (16, 16, 3), (256, 64, 4)],
+                         ids=["ks8", "ks8-ncrit256-depth2", "ks2-depth4", "ks1", "ks4-ncrit256-depth4"])
+def test_forces_every_kernel_setting(H, n_crit, tpg, depth):
+    # every sinks-per-lane variant (1, 2, 4, 8) and staging depth of the FP32 pair kernels against the oracle
+    st = ics.plummer(12000, 61)
+    P = plummer_params(12000, 1, n_crit=n_crit, threads_per_group=tpg, tile_depth=depth)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_build_tree(s)
+    ctx.hybrid_hard_force(s)
+    ctx.hybrid_soft_force(s)
+    torch.cuda.synchronize()
+    out = s.numpy()
+    T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
+    a_s, a_h, sc_s, sc_h = T.forces()
+    g_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+    g_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+    es = np.linalg.norm(g_s - a_s, axis=1) / np.linalg.norm(a_s, axis=1)
+    assert np.percentile(es, 99) <= 1e-5, np.percentile(es, 99)
+    nz = np.linalg.norm(a_h, axis=1) > 0
+    eh = np.linalg.norm(g_h - a_h, axis=1)[nz] / np.linalg.norm(a_h, axis=1)[nz]
+    assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
+    assert np.all(np.linalg.norm(g_h, axis=1)[~nz] == 0.0)
+
+
 def test_hard_lists_and_theta_zero(H):
     st = ics.plummer(3000, 4)
     for prec in (0, 1):
