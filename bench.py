@@ -59,6 +59,18 @@ def measured_peaks():
     return {}
 
 
+def job_rate(units_per_rank, seconds, dist=None, device="cuda"):
+    """Whole-job throughput of independent replicas: the units of all ranks over the slowest rank's time
+    (max over ranks). Returns (rate, max seconds)."""
+    if dist is None:
+        return units_per_rank / seconds, seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    tmax = float(t.item())
+    return dist.get_world_size() * units_per_rank / tmax, tmax
+
+
 def fp32_peak_tflops(nsm, sm_mhz):
     # 128 FP32 lanes per SM, 2 flops per FMA
     return nsm * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -569,11 +581,7 @@ def main():
     sort_ms, topo_ms, mom_ms, grp_ms = (ctx.hybrid_profile_read(k)[0] for k in (5, 6, 7, 8))
     ctx.hybrid_profile_read(0, reset=True)
     ctx.hybrid_profile(False)
-    if dist:
-        t = torch.tensor([t_steps], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_steps = float(t.item())
-    value = ws * w["n"] * args.steps / t_steps
+    value, t_steps = job_rate(w["n"] * args.steps, t_steps, dist)
     e_end = sum(ctx.hybrid_energy(s))
     energy = {"rel_drift": abs(e_end - e_start) / abs(e_start), "E_start": e_start, "E_end": e_end,
               "soft_steps": args.warmup + args.steps, "time": (args.warmup + args.steps) * w["dt_soft"]}
@@ -598,11 +606,8 @@ def main():
         e1.record(stream)
         barrier()
         te = e0.elapsed_time(e1) / 1e3
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": ws * w["n"] * ke / te, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+        e2e_value, te = job_rate(w["n"] * ke, te, dist)
+        e2e = {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                "steps": ke}
 
     # ---- roofline of the dominant kernel (soft pair, FP32 CUDA-core bound) ----
