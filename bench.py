@@ -217,7 +217,8 @@ def run_c4(args):
     def per(prec, kw):
         return hybrid.Params(precision=prec, **base, **kw)
 
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()           # a stream of its own: the library replays captured CUDA graphs on it
+    torch.cuda.set_stream(stream)
     # ---- batched FP32 ----
     ctx = hybrid.Context(per(1, specs[0][2]), stream)
     sysb = [hybrid.System(st, precision=1, ids=False, params=per(1, kw)) for st, (_, _, kw) in zip(states, specs)]
@@ -320,6 +321,7 @@ def run_c5(args):
                              n_leaf=16, n_crit=128, threads_per_group=32, precision=prec)
 
     budget = 150e9
+    torch.cuda.set_stream(torch.cuda.Stream())   # a stream of its own: captured CUDA graphs are replayed on it
     srv = hybrid.Server(rparams(1 << 16, 1), budget)
     # warm-up: one small request through the server (module load, first graph capture)
     srv.submit(count, ics.plummer(4096, 1), rparams(4096, 1), 2)
@@ -419,7 +421,8 @@ def run_c3(args):
     t_ic = time.perf_counter() - tic
     P = hybrid.Params(eps=eps, theta=0.4, R1=3 * eps, R2=6 * eps, dt_soft=1.0 / 128, n_hard=8, n_leaf=16,
                       n_crit=128, threads_per_group=32, precision=1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()           # a stream of its own: the library replays captured CUDA graphs on it
+    torch.cuda.set_stream(stream)
     ctx = hybrid.Context(P, stream)
     s = hybrid.System(st, precision=1, ids=False)
     chosen, _ = ctx.hybrid_autotune(s, [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0),
@@ -537,7 +540,8 @@ def main():
 
     P = hybrid.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
                       n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"], precision=1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()           # a stream of its own: the library replays captured CUDA graphs on it
+    torch.cuda.set_stream(stream)
     ctx = hybrid.Context(P, stream)
     st = ics.plummer(w["n"], w["seed"])
     s = hybrid.System(st, precision=1)
@@ -555,8 +559,9 @@ def main():
     # ---- device-timed region: inputs resident in HBM, L2 flushed before every step ----
     clocks = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    ctx.hybrid_profile(True)
-    ctx.hybrid_profile_read(0, reset=True)
+    ctx.hybrid_profile(1)                      # the pair kernels only: two event nodes per launch
+    for k in range(9):
+        ctx.hybrid_profile_read(k, reset=True)
     launches0 = ctx.hybrid_launch_count()
     inter_far = inter_near = 0
     barrier()
@@ -575,16 +580,20 @@ def main():
     t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     soft_ms, soft_n = ctx.hybrid_profile_read(0)
     hard_ms, hard_n = ctx.hybrid_profile_read(1)
-    walk_ms, walk_n = ctx.hybrid_profile_read(2)
-    tree_ms, tree_n = ctx.hybrid_profile_read(3)
-    integ_ms, integ_n = ctx.hybrid_profile_read(4)
-    sort_ms, topo_ms, mom_ms, grp_ms = (ctx.hybrid_profile_read(k)[0] for k in (5, 6, 7, 8))
+    ctx.hybrid_profile_read(0, reset=True)     # a reset clears every kind
+    # stage breakdown from a separate profiled pass (every stage bracketed: the brackets cost time)
+    kp = min(args.steps, 50)
+    ctx.hybrid_profile(2)
+    for _ in range(kp):
+        ctx.hybrid_step(s, 1)
+    torch.cuda.synchronize()
+    stage = [ctx.hybrid_profile_read(k)[0] / kp for k in range(9)]
     ctx.hybrid_profile_read(0, reset=True)
-    ctx.hybrid_profile(False)
+    ctx.hybrid_profile(0)
     value, t_steps = job_rate(w["n"] * args.steps, t_steps, dist)
     e_end = sum(ctx.hybrid_energy(s))
     energy = {"rel_drift": abs(e_end - e_start) / abs(e_start), "E_start": e_start, "E_end": e_end,
-              "soft_steps": args.warmup + args.steps, "time": (args.warmup + args.steps) * w["dt_soft"]}
+              "soft_steps": args.warmup + args.steps + kp, "time": (args.warmup + args.steps + kp) * w["dt_soft"]}
 
     # ---- end to end through the C-ABI with host buffers ----
     e2e = None
@@ -649,10 +658,12 @@ def main():
             "force_err_rms_vs_direct": ferr,
             "energy": energy,
             "kernel_ms_per_step": {"far_pair": soft_ms / args.steps, "near_pair": hard_ms / args.steps,
-                                   "walk": walk_ms / args.steps, "tree_build": tree_ms / args.steps,
-                                   "kick_drift": integ_ms / args.steps,
-                                   "tree_parts": {"sort": sort_ms / args.steps, "topology": topo_ms / args.steps,
-                                                  "moments": mom_ms / args.steps, "groups": grp_ms / args.steps}},
+                                   "walk": stage[2], "tree_build": stage[3], "kick_drift": stage[4],
+                                   "tree_parts": {"sort": stage[5], "topology": stage[6], "moments": stage[7],
+                                                  "groups": stage[8]},
+                                   "note": "far and near pair: the timed region; the other stages: a separate "
+                                           "pass of %d steps with every stage bracketed; topology and groups "
+                                           "run beside the permutation and the moments" % kp},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

@@ -199,11 +199,15 @@ hybrid_status hybrid_lists_copy(hybrid_ctx *ctx, int64_t *counts, int64_t *entri
  * pairs, the hard force the near pairs. */
 hybrid_status hybrid_interactions(hybrid_ctx *ctx, int64_t *far, int64_t *near);
 
-/* Profiling: when enabled, each stage is bracketed by CUDA events on the
- * context stream. hybrid_profile_read synchronises and returns, per kind
- * (0 far pair kernel, 1 near pair kernel, 2 walk, 3 tree build, 4 kick/drift,
- * 5 key sort, 6 tree topology, 7 moments, 8 groups; 5-8 are parts of 3), the
- * summed milliseconds and number of brackets since the last reset. */
+/* Profiling: enable = 1 brackets the pair kernels (kinds 0 and 1) with CUDA
+ * events on the context stream, enable = 2 every stage; 0 turns it off. In a
+ * replayed CUDA graph the brackets are event-record nodes of the graph. The
+ * tree-build parts run on two branches (topology and groups beside the
+ * permutation and the moments), so kinds 5-8 can overlap. hybrid_profile_read
+ * synchronises and returns, per kind (0 far pair kernel, 1 near pair kernel,
+ * 2 walk, 3 tree build, 4 kick/drift, 5 key sort, 6 tree topology, 7 moments,
+ * 8 groups; 5-8 are parts of 3), the summed milliseconds and number of
+ * brackets since the last reset. */
 hybrid_status hybrid_profile(hybrid_ctx *ctx, int enable);
 hybrid_status hybrid_profile_read(hybrid_ctx *ctx, int kind, double *ms, int64_t *launches, int reset);
 

@@ -113,6 +113,8 @@ enum ProfKind {
 struct hybrid_ctx {
     hybrid_params p{};
     cudaStream_t st = nullptr;
+    cudaStream_t st2 = nullptr;          // second branch of the tree build
+    cudaEvent_t ev_fork[2] = {nullptr, nullptr}, ev_join[2] = {nullptr, nullptr};
     int dev = 0, nsm = 0;
     std::string err;
     int64_t launches = 0;
@@ -158,7 +160,7 @@ struct hybrid_ctx {
     int last_walk_mode = 0;
 
     // profiling
-    bool prof = false;
+    int prof = 0;                          // 0 off, 1 pair kernels, 2 every stage
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     double prof_ms[hy::PROF_KINDS] = {0};
@@ -203,10 +205,12 @@ void scan_u64(hybrid_ctx *c, uint64_t *data, int64_t n_host, const int64_t *d_n,
 
 // ---- tree (tree.cu) ----
 void launch_box(hybrid_ctx *c);
-void launch_keys_sort_permute(hybrid_ctx *c);
-bool launch_build_levels(hybrid_ctx *c);
-void launch_moments(hybrid_ctx *c);
-void launch_groups(hybrid_ctx *c);
+void launch_keys_sort(hybrid_ctx *c);      // keys and their stable sort (keys[0], vals[0])
+void launch_permute(hybrid_ctx *c);        // state into key order, pair-kernel copies of the positions
+bool launch_build_levels(hybrid_ctx *c);   // topology from the sorted keys
+void launch_moments(hybrid_ctx *c);        // needs topology and the permuted state
+void launch_groups(hybrid_ctx *c);         // group table from the topology
+void launch_group_boxes(hybrid_ctx *c);    // needs the group table and the permuted state
 
 // ---- walk (walk.cu) ----
 void launch_walk(hybrid_ctx *c, int mode);   // mode bit 0 soft, bit 1 hard

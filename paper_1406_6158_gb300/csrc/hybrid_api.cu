@@ -53,11 +53,19 @@ void set_err(hybrid_ctx *c, const char *fmt, ...)
     c->err = buf;
 }
 
+// A profiling timestamp. Inside a stream capture a plain event record only
+// marks a dependency; the external flag makes it a record node of the graph.
+void prof_record(hybrid_ctx *c, cudaEvent_t e)
+{
+    if (c->capturing) cudaEventRecordWithFlags(e, c->st, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->st);
+}
+
 void prof_begin(hybrid_ctx *c, int kind, cudaEvent_t *e0)
 {
-    (void)kind;
     *e0 = nullptr;
     if (!c->prof) return;
+    if (c->prof == 1 && kind != PROF_SOFT && kind != PROF_HARD) return;   // level 1: the pair kernels only
     if (c->ev_pool.empty()) {
         cudaEvent_t e;
         cudaEventCreate(&e);
@@ -65,7 +73,7 @@ void prof_begin(hybrid_ctx *c, int kind, cudaEvent_t *e0)
     }
     *e0 = c->ev_pool.back();
     c->ev_pool.pop_back();
-    cudaEventRecord(*e0, c->st);
+    prof_record(c, *e0);
 }
 
 void prof_end(hybrid_ctx *c, int kind, cudaEvent_t e0)
@@ -78,7 +86,7 @@ void prof_end(hybrid_ctx *c, int kind, cudaEvent_t e0)
     }
     cudaEvent_t e1 = c->ev_pool.back();
     c->ev_pool.pop_back();
-    cudaEventRecord(e1, c->st);
+    prof_record(c, e1);
     c->ev_used.push_back({kind, {e0, e1}});
 }
 
@@ -354,22 +362,39 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
         launch_kick_seq(c, o.nk, o.which, o.kmode, o.val, o.dmode, o.dval);
         break;
     case OP_BUILD: {
+        // The build as a two-branch DAG: after the key sort, the topology and the group table (keys only)
+        // run beside the permutation of the state; then the group boxes beside the moments.
         cudaEvent_t e0 = nullptr;
         prof_begin(c, PROF_TREE, &e0);
         cudaEvent_t e1 = nullptr;
         prof_begin(c, PROF_SORT, &e1);
         launch_box(c);
-        launch_keys_sort_permute(c);
+        launch_keys_sort(c);
         prof_end(c, PROF_SORT, e1);
+        cudaStream_t main = c->st;
+        cudaEventRecord(c->ev_fork[0], main);
+        cudaStreamWaitEvent(c->st2, c->ev_fork[0], 0);
+        c->st = c->st2;
         prof_begin(c, PROF_TOPO, &e1);
         launch_build_levels(c);
         prof_end(c, PROF_TOPO, e1);
-        prof_begin(c, PROF_MOM, &e1);
-        launch_moments(c);
-        prof_end(c, PROF_MOM, e1);
         prof_begin(c, PROF_GROUPS, &e1);
         launch_groups(c);
         prof_end(c, PROF_GROUPS, e1);
+        cudaEventRecord(c->ev_join[0], c->st2);
+        c->st = main;
+        launch_permute(c);
+        cudaStreamWaitEvent(main, c->ev_join[0], 0);
+        cudaEventRecord(c->ev_fork[1], main);
+        cudaStreamWaitEvent(c->st2, c->ev_fork[1], 0);
+        c->st = c->st2;
+        launch_group_boxes(c);
+        cudaEventRecord(c->ev_join[1], c->st2);
+        c->st = main;
+        prof_begin(c, PROF_MOM, &e1);
+        launch_moments(c);
+        prof_end(c, PROF_MOM, e1);
+        cudaStreamWaitEvent(main, c->ev_join[1], 0);
         prof_end(c, PROF_TREE, e0);
         break;
     }
@@ -679,6 +704,15 @@ hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stre
         return HYBRID_ECUDA;
     }
     c->walk_warps = c->nsm * 32;
+    if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return HYBRID_ECUDA;
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaEventCreateWithFlags(&c->ev_fork[k], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&c->ev_join[k], cudaEventDisableTiming);
+    }
     {   // HYBRID_GRAPHS=0 enqueues every op directly instead of replaying captured CUDA graphs
         const char *g = getenv("HYBRID_GRAPHS");
         if (g && g[0] == '0') c->use_graphs = false;
@@ -735,6 +769,14 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
         cudaEventDestroy(u.second.second);
     }
     if (c->h_status) cudaFreeHost(c->h_status);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_fork[k]) cudaEventDestroy(c->ev_fork[k]);
+        if (c->ev_join[k]) cudaEventDestroy(c->ev_join[k]);
+    }
+    if (c->st2) {
+        cudaStreamSynchronize(c->st2);
+        cudaStreamDestroy(c->st2);
+    }
     delete c;
     return HYBRID_OK;
 }
@@ -1091,8 +1133,9 @@ hybrid_status hybrid_interactions(hybrid_ctx *c, int64_t *soft, int64_t *hard)
 hybrid_status hybrid_profile(hybrid_ctx *c, int enable)
 {
     if (!c) return HYBRID_EINVAL;
-    if (c->prof != (enable != 0)) drop_graphs(c);
-    c->prof = enable != 0;
+    const int level = enable == 0 ? 0 : (enable == 1 ? 1 : 2);
+    if (c->prof != level) drop_graphs(c);   // the brackets are part of the captured graphs
+    c->prof = level;
     return HYBRID_OK;
 }
 

@@ -1253,7 +1253,7 @@ void launch_box(hybrid_ctx *c)
     c->launches += 1;
 }
 
-void launch_keys_sort_permute(hybrid_ctx *c)
+void launch_keys_sort(hybrid_ctx *c)
 {
     Status *st = status_dev(c);
     const int64_t N = c->N;
@@ -1287,6 +1287,13 @@ void launch_keys_sort_permute(hybrid_ctx *c)
         std::swap(v0, v1);
     }
     // after 8 passes the sorted keys/values are back in buffer 0
+}
+
+void launch_permute(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    const int64_t N = c->N;
+    uint32_t *v0 = (uint32_t *)c->vals[0].p;
     PermArgs a;
     for (int f = 0; f < 7; ++f) {
         a.xin[f] = (const double *)c->x[f].p;
@@ -1440,11 +1447,18 @@ void launch_groups(hybrid_ctx *c)
         N, (const uint32_t *)c->gflag.p, (const uint32_t *)c->gscan.p, (const uint32_t *)c->ncount.p,
         (const int32_t *)c->psys.p, (uint32_t *)c->gnode.p, (uint32_t *)c->gfirst.p, (uint32_t *)c->gcount.p,
         (uint32_t *)c->gsys.p, d_tot, (int64_t *)c->ngroups_dev.p, st);
+    c->launches += 3;
+}
+
+void launch_group_boxes(hybrid_ctx *c)
+{
+    Status *st = status_dev(c);
+    const int64_t N = c->N;
     k_group_box<<<grid_for(c, N * 32 / 16, 256), 256, 0, c->st>>>(
         (const int64_t *)c->ngroups_dev.p, (const uint32_t *)c->gfirst.p, (const uint32_t *)c->gcount.p,
         (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const int32_t *)c->psys.p,
         (const SysBox *)c->box.p, (double *)c->glo.p, (double *)c->ghi.p, (GroupF *)c->gF.p, st);
-    c->launches += 4;
+    c->launches += 1;
 }
 
 }  // namespace hy

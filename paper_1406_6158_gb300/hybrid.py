@@ -280,8 +280,10 @@ class Context:
         self._check("hybrid_interactions", self.L.hybrid_interactions(self.h, C.byref(s), C.byref(h)))
         return s.value, h.value
 
-    def hybrid_profile(self, enable: bool):
-        self._check("hybrid_profile", self.L.hybrid_profile(self.h, int(bool(enable))))
+    def hybrid_profile(self, enable):
+        """True (or 2): every stage; 1: the pair kernels only; False (or 0): off."""
+        level = 2 if enable is True else (0 if enable is False else int(enable))
+        self._check("hybrid_profile", self.L.hybrid_profile(self.h, level))
 
     def hybrid_profile_read(self, kind: int, reset: bool = False):
         ms, n = C.c_double(), C.c_int64()

@@ -365,6 +365,35 @@ def test_autotune_choice_and_results(H):
             assert np.percentile(e, 99) <= 1e-5
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_graph_replay_equals_eager(H, prec):
+    # on a stream of its own the library captures each op sequence once (the tree build as a two-branch
+    # graph) and replays it; on the legacy default stream it launches eagerly: same results
+    st = ics.plummer(6000, 71)
+    P = plummer_params(6000, prec, n_hard=2)
+    runs = []
+    for stream in (None, torch.cuda.Stream()):
+        ctx = H.Context(P, stream)
+        s = H.System(st, precision=prec)
+        torch.cuda.synchronize()               # inputs made on the default stream are ready
+        for k in range(3):
+            ctx.hybrid_profile(k == 2)         # the last step also records the kernels' times
+            ctx.hybrid_step(s, 1)
+        torch.cuda.synchronize()
+        runs.append(s.numpy())
+        for kind in range(5):                  # far, near, walk, build, kicks: timed in both modes
+            ms, n = ctx.hybrid_profile_read(kind)
+            assert ms > 0.0 and n >= 1, (stream, kind)
+        ctx.close()
+    a, b = runs
+    assert np.array_equal(a["id"], b["id"])
+    for k in ("x", "y", "z", "vx", "vy", "vz"):
+        if prec == 0:
+            assert np.array_equal(a[k], b[k]), k
+        else:
+            assert np.max(np.abs(a[k] - b[k])) <= 1e-9 * max(1.0, np.max(np.abs(a[k]))), k
+
+
 def test_kick_drift_calls(H):
     st = ics.plummer(1000, 30)
     P = plummer_params(1000, 0)
