@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 N_DEFAULT = 1 << 17
 METRIC = "particle-steps/s"
 FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul, 3 fma (by convention 20)
+# DRAM bytes (read + write) of one far-pair launch on this workload, from an ncu capture of the kernel
+# variant the key names (n_crit, threads per group, staging depth); see profiles/far_pair_plummer131k.md.
+# Reported as the roofline's traffic only when the autotuner picks that same variant.
+FAR_TRAFFIC_BYTES = {(128, 32, 4): 56.934e6}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -627,8 +631,9 @@ def main():
     soft_avg_s = (soft_ms / 1e3) / max(soft_n, 1)
     per_launch_flops = FLOPS_PER_INTERACTION * inter_far / max(args.steps, 1)
     achieved = per_launch_flops / soft_avg_s / 1e12 if soft_avg_s > 0 else None
+    traffic = args.traffic_bytes if args.traffic_bytes is not None else FAR_TRAFFIC_BYTES.get(tuple(chosen))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if achieved else None, "traffic": args.traffic_bytes,
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "kernel": "k_pair_f32 far (cells + far particles, soft force)",
                 "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
                              (props.multi_processor_count, sm_max)}
