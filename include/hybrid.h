@@ -164,6 +164,14 @@ hybrid_status hybrid_autotune(hybrid_ctx *ctx, hybrid_system *sys, int n_sys, co
  * order within its system, of the particle now at position k. */
 hybrid_status hybrid_get_perm(hybrid_ctx *ctx, int32_t *dev_perm);
 
+/* Self-test of failure detection (not part of the method): the library's one
+ * device-side wait (the key sort's look-back) is bounded, records
+ * HYBRID_ETIMEOUT when its polls run out and lets the kernel finish. This call
+ * runs that wait, with max_polls polls, on a flag that nothing sets, then
+ * returns what hybrid_sync returns: HYBRID_ETIMEOUT, with the context still
+ * usable. EINVAL for max_polls < 1. */
+hybrid_status hybrid_selftest_wait(hybrid_ctx *ctx, int32_t max_polls);
+
 /* Waits for the context's stream and returns the first device-side failure
  * recorded since the last check (and clears it). */
 hybrid_status hybrid_sync(hybrid_ctx *ctx);

@@ -211,6 +211,7 @@ bool launch_build_levels(hybrid_ctx *c);   // topology from the sorted keys
 void launch_moments(hybrid_ctx *c);        // needs topology and the permuted state
 void launch_groups(hybrid_ctx *c);         // group table from the topology
 void launch_group_boxes(hybrid_ctx *c);    // needs the group table and the permuted state
+void launch_wait_selftest(hybrid_ctx *c, int max_polls);   // a bounded wait on a flag nothing sets
 
 // ---- walk (walk.cu) ----
 void launch_walk(hybrid_ctx *c, int mode);   // mode bit 0 soft, bit 1 hard

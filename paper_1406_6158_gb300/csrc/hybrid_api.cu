@@ -943,6 +943,15 @@ hybrid_status hybrid_autotune(hybrid_ctx *c, hybrid_system *sys, int n_sys, cons
     return finish(c, r);
 }
 
+hybrid_status hybrid_selftest_wait(hybrid_ctx *c, int32_t max_polls)
+{
+    if (!c || max_polls < 1) return HYBRID_EINVAL;
+    launch_wait_selftest(c, max_polls);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "kernel launch");
+    return hybrid_sync(c);
+}
+
 hybrid_status hybrid_get_perm(hybrid_ctx *c, int32_t *dev_perm)
 {
     if (!c || !dev_perm || c->N == 0) return HYBRID_EINVAL;

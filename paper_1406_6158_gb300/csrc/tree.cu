@@ -197,6 +197,30 @@ __device__ __forceinline__ void st_relaxed_u32(uint32_t *p, uint32_t v)
     asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Polls *q until one of the flag bits is set, at most max_polls times with a
+// short sleep in between; when the polls run out it records HYBRID_ETIMEOUT in
+// the status block and returns dflt, so the caller finishes without waiting.
+__device__ __forceinline__ uint32_t wait_flagged(const uint32_t *q, uint32_t flags, int max_polls, Status *st,
+                                                 uint32_t dflt)
+{
+    uint32_t v = ld_relaxed_u32(q);
+    for (int spins = 0; (v & flags) == 0u; ++spins) {
+        if (spins >= max_polls) {
+            fail(st, HYBRID_ETIMEOUT, -1);
+            return dflt;
+        }
+        __nanosleep(64);
+        v = ld_relaxed_u32(q);
+    }
+    return v;
+}
+
+// Self-test of the bounded wait: one thread waits for a flag that nothing sets.
+__global__ void k_wait_selftest(const uint32_t *word, int max_polls, Status *st)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)wait_flagged(word, 1u, max_polls, st, 0u);
+}
+
 __global__ void __launch_bounds__(256) k_digit_counts(const uint64_t *__restrict__ key, const Chunk *__restrict__ chunks,
                                                       int nchunks, uint32_t *__restrict__ counts)
 {
@@ -282,17 +306,7 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
         if (!first) {
             for (int j = c - 1; j >= ch.first_chunk; --j) {
                 const uint32_t *q = look + (size_t)j * 256 + d;
-                uint32_t vq = ld_relaxed_u32(q);
-                int spins = 0;
-                while ((vq & (LB_AGG | LB_INC)) == 0u) {
-                    if (++spins > LB_SPIN_MAX) {
-                        fail(st, 5, -1);   // HYBRID_ETIMEOUT
-                        vq = LB_INC;
-                        break;
-                    }
-                    __nanosleep(64);
-                    vq = ld_relaxed_u32(q);
-                }
+                const uint32_t vq = wait_flagged(q, LB_AGG | LB_INC, LB_SPIN_MAX, st, LB_INC);
                 excl += vq & LB_CNT;
                 if (vq & LB_INC) break;
             }
@@ -1459,6 +1473,14 @@ void launch_group_boxes(hybrid_ctx *c)
         (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const int32_t *)c->psys.p,
         (const SysBox *)c->box.p, (double *)c->glo.p, (double *)c->ghi.p, (GroupF *)c->gF.p, st);
     c->launches += 1;
+}
+
+void launch_wait_selftest(hybrid_ctx *c, int max_polls)
+{
+    uint32_t *word = (uint32_t *)((unsigned long long *)c->counter.p + 15);   // a slot nothing else uses
+    cudaMemsetAsync(word, 0, sizeof(uint32_t), c->st);
+    k_wait_selftest<<<1, 32, 0, c->st>>>(word, max_polls, status_dev(c));
+    c->launches++;
 }
 
 }  // namespace hy

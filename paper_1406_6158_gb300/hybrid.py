@@ -28,7 +28,7 @@ EXPORTS = (
     "hybrid_kick", "hybrid_drift", "hybrid_step", "hybrid_step_batched", "hybrid_get_perm", "hybrid_sync",
     "hybrid_last_error", "hybrid_tree_info", "hybrid_tree_copy", "hybrid_lists_copy", "hybrid_interactions",
     "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy", "hybrid_energy_noalloc",
-    "hybrid_autotune", "hybrid_server_create", "hybrid_server_destroy", "hybrid_server_submit",
+    "hybrid_autotune", "hybrid_selftest_wait", "hybrid_server_create", "hybrid_server_destroy", "hybrid_server_submit",
     "hybrid_server_step", "hybrid_server_next", "hybrid_server_used_bytes", "hybrid_server_last_error",
 )
 SERVER_BYTES_PER_PARTICLE = 1536
@@ -97,6 +97,7 @@ def load() -> C.CDLL:
         "hybrid_energy": [ctx, sysp, P(D), P(D)],
         "hybrid_energy_noalloc": [I64, VP, VP, VP, VP, VP, VP, VP, D, D, VP, P(D), P(D)],
         "hybrid_autotune": [ctx, sysp, C.c_int, VP, C.c_int, VP, P(I32)],
+        "hybrid_selftest_wait": [ctx, I32],
         "hybrid_server_create": [P(VP), P(hybrid_params), D, VP],
         "hybrid_server_destroy": [VP],
         "hybrid_server_submit": [VP, I64, I64, VP, VP, VP, VP, VP, VP, VP, P(hybrid_params), I32],
@@ -290,6 +291,10 @@ class Context:
         self._check("hybrid_profile_read", self.L.hybrid_profile_read(self.h, kind, C.byref(ms), C.byref(n),
                                                                       int(bool(reset))))
         return ms.value, n.value
+
+    def hybrid_selftest_wait(self, max_polls: int) -> int:
+        """Runs the bounded device wait on a flag nothing sets; returns the status code (ETIMEOUT expected)."""
+        return int(self.L.hybrid_selftest_wait(self.h, int(max_polls)))
 
     def hybrid_launch_count(self) -> int:
         return int(self.L.hybrid_launch_count(self.h))

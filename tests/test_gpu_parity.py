@@ -394,6 +394,20 @@ def test_graph_replay_equals_eager(H, prec):
             assert np.max(np.abs(a[k] - b[k])) <= 1e-9 * max(1.0, np.max(np.abs(a[k]))), k
 
 
+def test_bounded_wait_times_out_and_context_survives(H):
+    # failure detection without a fault: a device wait on a flag nothing sets gives up after its polls,
+    # the host reads HYBRID_ETIMEOUT, and the same context then steps normally
+    st = ics.plummer(2000, 81)
+    P = plummer_params(2000, 1)
+    ctx = H.Context(P)
+    assert ctx.hybrid_selftest_wait(1000) == H.ETIMEOUT
+    assert ctx.hybrid_selftest_wait(1000) == H.ETIMEOUT      # the status was cleared and is raised again
+    s = H.System(st, precision=1)
+    ctx.hybrid_step(s, 1)
+    ctx.hybrid_sync()
+    assert np.all(np.isfinite(s.numpy()["x"]))
+
+
 def test_kick_drift_calls(H):
     st = ics.plummer(1000, 30)
     P = plummer_params(1000, 0)
