@@ -395,32 +395,51 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
             const bool soft_leaf = valid && leaf && open_s && !near;
             const bool hard_leaf = valid && leaf && (open_s || open_h) && near;
             const bool open = valid && !leaf && (open_s || open_h);
+            // per-lane counts of far particles, near particles and children, packed 10 bits each when every
+            // count is below 32 (one scan instead of three); cells take one ballot
+            const uint32_t kf = soft_leaf ? T.w : 0u, kn = hard_leaf ? T.w : 0u, kc = open ? T.y : 0u;
+            const bool small = __all_sync(0xffffffffu, kf < 32u && kn < 32u);
+            uint32_t exf, exn, exc, totf, totn, totc;
+            if (small) {
+                uint32_t tp;
+                const uint32_t ep = warp_excl_scan(kf | (kn << 10) | (kc << 20), tp);
+                exf = ep & 1023u;
+                exn = (ep >> 10) & 1023u;
+                exc = ep >> 20;
+                totf = tp & 1023u;
+                totn = (tp >> 10) & 1023u;
+                totc = tp >> 20;
+            } else {
+                exf = warp_excl_scan(kf, totf);
+                exn = warp_excl_scan(kn, totn);
+                exc = warp_excl_scan(kc, totc);
+            }
+            {
+                const unsigned bm = __ballot_sync(0xffffffffu, take_cell);
+                const uint32_t totk[3] = {(uint32_t)__popc(bm), totf, totn};
 #pragma unroll
-            for (int t = 0; t < 3; ++t) {   // cells, far particles, near particles
-                const bool on = t == 0 ? take_cell : (t == 1 ? soft_leaf : hard_leaf);
-                uint32_t tot;
-                const uint32_t k = on ? (t == 0 ? 1u : T.w) : 0u;
-                const uint32_t ex = warp_excl_scan(k, tot);
-                if (tot) {
-                    const uint64_t pos = reserve(t, tot);
-                    if (pos == ~0ull) break;
-                    if (on) {
-                        uint32_t *dst = a.list + pos + ex;
-                        if (t == 0) dst[0] = c;
-                        else
+                for (int t = 0; t < 3; ++t) {   // cells, far particles, near particles
+                    const uint32_t tot = totk[t];
+                    if (tot) {
+                        const uint64_t pos = reserve(t, tot);
+                        if (pos == ~0ull) break;
+                        if (t == 0) {
+                            if (take_cell) a.list[pos + __popc(bm & ((1u << lane) - 1u))] = c;
+                        } else {
+                            const uint32_t k = t == 1 ? kf : kn;
+                            uint32_t *dst = a.list + pos + (t == 1 ? exf : exn);
                             for (uint32_t j = 0; j < k; ++j) dst[j] = T.z + j;
-                    }
-                    if (lane == t) {
-                        my_cur = pos + tot;
-                        my_len += tot;
+                        }
+                        if (lane == t) {
+                            my_cur = pos + tot;
+                            my_len += tot;
+                        }
                     }
                 }
             }
             if (fail_list || fail_items) break;
             {   // children of opened cells
-                uint32_t tot;
-                const uint32_t k = open ? T.y : 0u;
-                const uint32_t ex = warp_excl_scan(k, tot);
+                const uint32_t tot = totc, k = kc, ex = exc;
                 if (sp + (int)tot > WALK_SSTK) {   // move the shared part under the global part
                     if (gp + sp > a.cap_stack) {
                         overflow = true;
