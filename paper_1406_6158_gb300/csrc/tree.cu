@@ -713,13 +713,16 @@ struct MomSumsF {
     float M, sx, sy, sz, Q;
 };
 
+// G lanes (a whole warp, G = 32, or an aligned group of G = 8 lanes with
+// member mask gm; sl = lane within the group) sum a particle range.
+template <int G>
 __device__ __forceinline__ MomSumsF mom_range_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo,
-                                                  uint32_t f, uint32_t n, uint32_t ref, int lane)
+                                                  uint32_t f, uint32_t n, uint32_t ref, int sl, unsigned gm)
 {
     const float4 hr = phi[ref], lr = plo[ref];
     MomSumsF r = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll 4
-    for (uint32_t i = f + lane; i < f + n; i += 32) {
+    for (uint32_t i = f + sl; i < f + n; i += G) {
         const float4 h = phi[i], l = plo[i];
         const float d0 = (h.x - hr.x) + (l.x - lr.x), d1 = (h.y - hr.y) + (l.y - lr.y), d2 = (h.z - hr.z) + (l.z - lr.z);
         const float mi = h.w;
@@ -730,12 +733,12 @@ __device__ __forceinline__ MomSumsF mom_range_f32(const float4 *__restrict__ phi
         r.Q = fmaf(mi, fmaf(d0, d0, fmaf(d1, d1, d2 * d2)), r.Q);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        r.M += __shfl_xor_sync(0xffffffffu, r.M, o);
-        r.sx += __shfl_xor_sync(0xffffffffu, r.sx, o);
-        r.sy += __shfl_xor_sync(0xffffffffu, r.sy, o);
-        r.sz += __shfl_xor_sync(0xffffffffu, r.sz, o);
-        r.Q += __shfl_xor_sync(0xffffffffu, r.Q, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+        r.M += __shfl_xor_sync(gm, r.M, o, G);
+        r.sx += __shfl_xor_sync(gm, r.sx, o, G);
+        r.sy += __shfl_xor_sync(gm, r.sy, o, G);
+        r.sz += __shfl_xor_sync(gm, r.sz, o, G);
+        r.Q += __shfl_xor_sync(gm, r.Q, o, G);
     }
     return r;
 }
@@ -756,14 +759,15 @@ __device__ __forceinline__ void mom_store_f32(const MomArgs &a, uint32_t c, uint
 
 // B2 of a small cell about its centre of mass e (offsets from particle ref),
 // summed directly so that no M|e|^2 cancels against the second moment, and
-// b_max, the largest distance of its particles to e.
+// b_max, the largest distance of its particles to e (G lanes as above).
+template <int G>
 __device__ __forceinline__ void mom_b2_f32(const float4 *__restrict__ phi, const float4 *__restrict__ plo, uint32_t f,
-                                           uint32_t n, uint32_t ref, float e0, float e1, float e2, int lane, float &B2,
-                                           float &bmax)
+                                           uint32_t n, uint32_t ref, float e0, float e1, float e2, int sl, unsigned gm,
+                                           float &B2, float &bmax)
 {
     const float4 hr = phi[ref], lr = plo[ref];
     float q = 0.0f, d2max = 0.0f;
-    for (uint32_t i = f + lane; i < f + n; i += 32) {
+    for (uint32_t i = f + sl; i < f + n; i += G) {
         const float4 h = phi[i], l = plo[i];
         const float d0 = ((h.x - hr.x) + (l.x - lr.x)) - e0, d1 = ((h.y - hr.y) + (l.y - lr.y)) - e1,
                     d2 = ((h.z - hr.z) + (l.z - lr.z)) - e2;
@@ -772,9 +776,9 @@ __device__ __forceinline__ void mom_b2_f32(const float4 *__restrict__ phi, const
         d2max = fmaxf(d2max, r2);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        q += __shfl_xor_sync(0xffffffffu, q, o);
-        d2max = fmaxf(d2max, __shfl_xor_sync(0xffffffffu, d2max, o));
+    for (int o = G / 2; o > 0; o >>= 1) {
+        q += __shfl_xor_sync(gm, q, o, G);
+        d2max = fmaxf(d2max, __shfl_xor_sync(gm, d2max, o, G));
     }
     B2 = q;
     bmax = sqrtf(d2max);
@@ -834,108 +838,116 @@ __device__ __forceinline__ double warp_sum_d(double v)
 }
 
 // A larger cell from its (at most 8) children, one per lane, in a fixed order.
-// FP64 form in FP64. FP32 form in FP32 on offsets from the first child's
-// hi/lo centre of mass (hi differences exact), stored like a small cell's.
-template <bool F64>
-__device__ void mom_combine(const MomArgs &a, uint32_t c, int lane)
+// FP64 form in FP64 (a whole warp). FP32 form in FP32 on offsets from the
+// first child's hi/lo centre of mass (hi differences exact), stored like a
+// small cell's, by G lanes (a warp or an aligned group of 8 with mask gm).
+__device__ void mom_combine_f64(const MomArgs &a, uint32_t c, int lane)
 {
     const uint32_t ch0 = a.nchild[c], k = a.nnch[c];
     const uint32_t f = a.nfirst[c];
     const SysBox &b = a.box[a.psys[f]];
     const bool on = (uint32_t)lane < k;
-    if (F64) {
-        double M = 0.0, x = 0.0, y = 0.0, z = 0.0, B2 = 0.0;
-        if (on) {
-            const uint32_t j = ch0 + lane;
-            M = __ldcg(a.M + j);
-            x = __ldcg(a.cx + j);
-            y = __ldcg(a.cy + j);
-            z = __ldcg(a.cz + j);
-            B2 = __ldcg(a.B2 + j);
-        }
-        const double rx = __shfl_sync(0xffffffffu, x, 0), ry = __shfl_sync(0xffffffffu, y, 0),
-                     rz = __shfl_sync(0xffffffffu, z, 0);
-        const double dx = x - rx, dy = y - ry, dz = z - rz;
-        const double Mt = warp_sum_d(M);
-        double c0, c1, c2, B2t = 0.0;
-        if (Mt > 0.0) {
-            const double ex = warp_sum_d(M * dx) / Mt, ey = warp_sum_d(M * dy) / Mt, ez = warp_sum_d(M * dz) / Mt;
-            c0 = rx + ex;
-            c1 = ry + ey;
-            c2 = rz + ez;
-            const double qx = dx - ex, qy = dy - ey, qz = dz - ez;
-            B2t = warp_sum_d(on ? B2 + M * (qx * qx + qy * qy + qz * qz) : 0.0);
-        } else {   // massless cell: its geometric centre
-            double o[3], sd;
-            cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
-            c0 = o[0] + 0.5 * sd;
-            c1 = o[1] + 0.5 * sd;
-            c2 = o[2] + 0.5 * sd;
-        }
-        if (lane == 0) store_com(a, c, Mt, c0, c1, c2, B2t);
-    } else {
-        float4 A = make_float4(0.0f, 0.0f, 0.0f, 0.0f), B = A;
-        if (on) {
-            A = __ldcg(a.nA + ch0 + lane);
-            B = __ldcg(a.nB + ch0 + lane);
-        }
-        const float hx = __shfl_sync(0xffffffffu, A.x, 0), hy = __shfl_sync(0xffffffffu, A.y, 0),
-                    hz = __shfl_sync(0xffffffffu, A.z, 0);
-        const float lx = __shfl_sync(0xffffffffu, B.x, 0), ly = __shfl_sync(0xffffffffu, B.y, 0),
-                    lz = __shfl_sync(0xffffffffu, B.z, 0);
-        const float M = A.w, dx = (A.x - hx) + (B.x - lx), dy = (A.y - hy) + (B.y - ly), dz = (A.z - hz) + (B.z - lz);
-        float Mt = M, sx = M * dx, sy = M * dy, sz = M * dz;
+    double M = 0.0, x = 0.0, y = 0.0, z = 0.0, B2 = 0.0;
+    if (on) {
+        const uint32_t j = ch0 + lane;
+        M = __ldcg(a.M + j);
+        x = __ldcg(a.cx + j);
+        y = __ldcg(a.cy + j);
+        z = __ldcg(a.cz + j);
+        B2 = __ldcg(a.B2 + j);
+    }
+    const double rx = __shfl_sync(0xffffffffu, x, 0), ry = __shfl_sync(0xffffffffu, y, 0),
+                 rz = __shfl_sync(0xffffffffu, z, 0);
+    const double dx = x - rx, dy = y - ry, dz = z - rz;
+    const double Mt = warp_sum_d(M);
+    double c0, c1, c2, B2t = 0.0;
+    if (Mt > 0.0) {
+        const double ex = warp_sum_d(M * dx) / Mt, ey = warp_sum_d(M * dy) / Mt, ez = warp_sum_d(M * dz) / Mt;
+        c0 = rx + ex;
+        c1 = ry + ey;
+        c2 = rz + ez;
+        const double qx = dx - ex, qy = dy - ey, qz = dz - ez;
+        B2t = warp_sum_d(on ? B2 + M * (qx * qx + qy * qy + qz * qz) : 0.0);
+    } else {   // massless cell: its geometric centre
+        double o[3], sd;
+        cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
+        c0 = o[0] + 0.5 * sd;
+        c1 = o[1] + 0.5 * sd;
+        c2 = o[2] + 0.5 * sd;
+    }
+    if (lane == 0) store_com(a, c, Mt, c0, c1, c2, B2t);
+}
+
+template <int G>
+__device__ void mom_combine_f32(const MomArgs &a, uint32_t c, int lane, unsigned gm)
+{
+    const uint32_t ch0 = a.nchild[c], k = a.nnch[c];
+    const uint32_t f = a.nfirst[c];
+    const SysBox &b = a.box[a.psys[f]];
+    const bool on = (uint32_t)lane < k;
+    float4 A = make_float4(0.0f, 0.0f, 0.0f, 0.0f), B = A;
+    if (on) {
+        A = __ldcg(a.nA + ch0 + lane);
+        B = __ldcg(a.nB + ch0 + lane);
+    }
+    const float hx = __shfl_sync(gm, A.x, 0, G), hy = __shfl_sync(gm, A.y, 0, G),
+                hz = __shfl_sync(gm, A.z, 0, G);
+    const float lx = __shfl_sync(gm, B.x, 0, G), ly = __shfl_sync(gm, B.y, 0, G),
+                lz = __shfl_sync(gm, B.z, 0, G);
+    const float M = A.w, dx = (A.x - hx) + (B.x - lx), dy = (A.y - hy) + (B.y - ly), dz = (A.z - hz) + (B.z - lz);
+    float Mt = M, sx = M * dx, sy = M * dy, sz = M * dz;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            Mt += __shfl_xor_sync(0xffffffffu, Mt, o);
-            sx += __shfl_xor_sync(0xffffffffu, sx, o);
-            sy += __shfl_xor_sync(0xffffffffu, sy, o);
-            sz += __shfl_xor_sync(0xffffffffu, sz, o);
-        }
-        float e0, e1, e2, B2t = 0.0f;
-        if (Mt > 0.0f) {
-            e0 = sx / Mt;
-            e1 = sy / Mt;
-            e2 = sz / Mt;
-            const float qx = dx - e0, qy = dy - e1, qz = dz - e2;
-            B2t = on ? fmaf(M, qx * qx + qy * qy + qz * qz, B.w) : 0.0f;
+    for (int o = G / 2; o > 0; o >>= 1) {
+        Mt += __shfl_xor_sync(gm, Mt, o, G);
+        sx += __shfl_xor_sync(gm, sx, o, G);
+        sy += __shfl_xor_sync(gm, sy, o, G);
+        sz += __shfl_xor_sync(gm, sz, o, G);
+    }
+    float e0, e1, e2, B2t = 0.0f;
+    if (Mt > 0.0f) {
+        e0 = sx / Mt;
+        e1 = sy / Mt;
+        e2 = sz / Mt;
+        const float qx = dx - e0, qy = dy - e1, qz = dz - e2;
+        B2t = on ? fmaf(M, qx * qx + qy * qy + qz * qz, B.w) : 0.0f;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) B2t += __shfl_xor_sync(0xffffffffu, B2t, o);
-        } else {   // massless cell: its geometric centre, relative to the first child's centre
-            double o[3], sd;
-            cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
-            e0 = (float)((o[0] + 0.5 * sd - b.lo[0]) - ((double)hx + (double)lx));
-            e1 = (float)((o[1] + 0.5 * sd - b.lo[1]) - ((double)hy + (double)ly));
-            e2 = (float)((o[2] + 0.5 * sd - b.lo[2]) - ((double)hz + (double)lz));
-        }
-        if (lane == 0) {
-            const float t0 = lx + e0, t1 = ly + e1, t2 = lz + e2;
-            const float g0 = rintf(t0 * b.inv_uf) * b.uf, g1 = rintf(t1 * b.inv_uf) * b.uf,
-                        g2 = rintf(t2 * b.inv_uf) * b.uf;
-            a.nA[c] = make_float4(hx + g0, hy + g1, hz + g2, Mt);
-            a.nB[c] = make_float4(t0 - g0, t1 - g1, t2 - g2, B2t);
-        }
+        for (int o = G / 2; o > 0; o >>= 1) B2t += __shfl_xor_sync(gm, B2t, o, G);
+    } else {   // massless cell: its geometric centre, relative to the first child's centre
+        double o[3], sd;
+        cell_geom(b, a.key[f], a.nlevel[c], o, &sd);
+        e0 = (float)((o[0] + 0.5 * sd - b.lo[0]) - ((double)hx + (double)lx));
+        e1 = (float)((o[1] + 0.5 * sd - b.lo[1]) - ((double)hy + (double)ly));
+        e2 = (float)((o[2] + 0.5 * sd - b.lo[2]) - ((double)hz + (double)lz));
+    }
+    if (lane == 0) {
+        const float t0 = lx + e0, t1 = ly + e1, t2 = lz + e2;
+        const float g0 = rintf(t0 * b.inv_uf) * b.uf, g1 = rintf(t1 * b.inv_uf) * b.uf,
+                    g2 = rintf(t2 * b.inv_uf) * b.uf;
+        a.nA[c] = make_float4(hx + g0, hy + g1, hz + g2, Mt);
+        a.nB[c] = make_float4(t0 - g0, t1 - g1, t2 - g2, B2t);
     }
 }
 
 // After cell c is final: if its parent is a larger cell and c is the last of
-// its children to finish, combine the parent, and so on upwards.
-template <bool F64>
-__device__ void mom_climb(const MomArgs &a, uint32_t c, int lane)
+// its children to finish, combine the parent, and so on upwards. G lanes (a
+// warp, or an aligned group of 8 with mask gm; lane = lane within the group).
+template <bool F64, int G>
+__device__ void mom_climb(const MomArgs &a, uint32_t c, int lane, unsigned gm)
 {
     for (;;) {
         const uint32_t p = a.nparent[c];
         if (p == NONE || a.ncount[p] <= MOM_CH) return;
-        __syncwarp();
+        __syncwarp(gm);
         unsigned int old = 0;
         if (lane == 0) {   // release: c's moments (stored by this lane) before the count; acquire: the others' after
             cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(a.done[p]);
             old = cnt.fetch_add(1u, cuda::memory_order_acq_rel);
         }
-        old = __shfl_sync(0xffffffffu, old, 0);
+        old = __shfl_sync(gm, old, 0, G);
         if (old + 1u != a.nnch[p]) return;
-        __syncwarp();
-        mom_combine<F64>(a, p, lane);
+        __syncwarp(gm);
+        if (F64) mom_combine_f64(a, p, lane);
+        else mom_combine_f32<G>(a, p, lane, gm);
         c = p;
     }
 }
@@ -953,10 +965,11 @@ __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long
     const uint32_t total = a.lvl[LEVELS + 1];
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
-        const uint32_t f = a.nfirst[c], n = a.ncount[c];
-        if (n <= MOM_CH || a.nnch[c] == 0) {
-            if (F64) {
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (F64) {   // one warp per cell
+        for (uint32_t c = warp; c < total; c += nw) {
+            const uint32_t f = a.nfirst[c], n = a.ncount[c];
+            if (n <= MOM_CH || a.nnch[c] == 0) {
                 const double o0 = a.x[f], o1 = a.y[f], o2 = a.z[f];
                 const MomSums r = mom_range(a, f, n, o0, o1, o2, lane);
                 if (lane == 0) mom_store(a, c, r, o0, o1, o2);
@@ -972,27 +985,47 @@ __global__ void __launch_bounds__(256) k_mom_small(MomArgs a, unsigned long long
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) dm = fmax(dm, __shfl_xor_sync(0xffffffffu, dm, o));
                 if (lane == 0) a.bmax64[c] = (unsigned long long)__double_as_longlong(dm);
-            } else {
-                const MomSumsF r = mom_range_f32(a.phi, a.plo, f, n, f, lane);
+                mom_climb<true, 32>(a, c, lane, 0xffffffffu);
+            } else if (lane == 0) {
+                const uint32_t nch = (n + BM_CH - 1) / BM_CH;
+                const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
+                if (base + nch > cap_items) {
+                    fail(st, HYBRID_ECAPACITY, where);
+                    continue;
+                }
+                bigbase[c] = (uint32_t)base;
+                for (uint32_t k = 0; k < nch; ++k) items[base + k] = c;
+            }
+        }
+    } else {   // FP32 form: four cells per warp, eight lanes each (most cells are leaves of a few particles)
+        const int sub = lane >> 3, sl = lane & 7;
+        const unsigned gm = 0xFFu << (8 * sub);
+        const uint32_t nq = (total + 3) / 4;
+        for (uint32_t q = warp; q < nq; q += nw) {
+            const uint32_t c = 4 * q + sub;
+            if (c >= total) continue;
+            const uint32_t f = a.nfirst[c], n = a.ncount[c];
+            if (n <= MOM_CH || a.nnch[c] == 0) {
+                const MomSumsF r = mom_range_f32<8>(a.phi, a.plo, f, n, f, sl, gm);
                 const float iM = r.M > 0.0f ? 1.0f / r.M : 0.0f;
                 const float e0 = r.sx * iM, e1 = r.sy * iM, e2 = r.sz * iM;
                 float B2, bm;
-                mom_b2_f32(a.phi, a.plo, f, n, f, e0, e1, e2, lane, B2, bm);
-                if (lane == 0) {
+                mom_b2_f32<8>(a.phi, a.plo, f, n, f, e0, e1, e2, sl, gm, B2, bm);
+                if (sl == 0) {
                     mom_store_f32(a, c, f, r.M, e0, e1, e2, B2);
                     a.bmax32[c] = __float_as_uint(bm);
                 }
+                mom_climb<false, 8>(a, c, sl, gm);
+            } else if (sl == 0) {
+                const uint32_t nch = (n + BM_CH - 1) / BM_CH;
+                const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
+                if (base + nch > cap_items) {
+                    fail(st, HYBRID_ECAPACITY, where);
+                    continue;
+                }
+                bigbase[c] = (uint32_t)base;
+                for (uint32_t k = 0; k < nch; ++k) items[base + k] = c;
             }
-            mom_climb<F64>(a, c, lane);
-        } else if (lane == 0) {
-            const uint32_t nch = (n + BM_CH - 1) / BM_CH;
-            const unsigned long long base = atomicAdd(nitems, (unsigned long long)nch);
-            if (base + nch > cap_items) {
-                fail(st, HYBRID_ECAPACITY, where);
-                continue;
-            }
-            bigbase[c] = (uint32_t)base;
-            for (uint32_t k = 0; k < nch; ++k) items[base + k] = c;
         }
     }
 }
