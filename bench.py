@@ -35,6 +35,7 @@ FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul,
 # Reported as the roofline's traffic only when the autotuner picks that same variant.
 FAR_TRAFFIC_BYTES = {(128, 32, 4): 56.934e6}
 L2_FLUSH_BYTES = 256 << 20
+ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
 
 
 def workload(n):
@@ -488,6 +489,125 @@ def run_c3(args):
     return 0
 
 
+def paper_params(n):
+    """The paper's parameter set for the Plummer model (Sec. IV-A): eps = 0.1 N^-0.26, dt_h = eps / sigma_v with
+    sigma_v = 0.65, n = 4 hard steps per soft step, R1 = 1.03 N^-1/3, R2 = 2 R1, absolute MAC with a_err = 2^-8."""
+    eps = 0.1 * n ** -0.26
+    R1 = 1.03 * n ** (-1.0 / 3.0)
+    return dict(eps=eps, dt_h=eps / 0.65, R1=R1, R2=2 * R1, a_err=2.0 ** -8, n_hard=4)
+
+
+def run_paper(args):
+    """Hybrid against normal tree on one GPU with the paper's parameters (Sec. IV-B, IV-D, Eq. 16).
+
+    Three contexts on the same Plummer sphere, each autotuned, FP32 pairs on FP64 state:
+      hybrid  n = 4 (one soft step and three hard steps per dt_s = 4 dt_h)      -> T_hybrid per dt_s
+      soft    n = 1, dt_s = dt_h (the soft step alone)                          -> T_soft
+      normal  R1 = R2 = 0 (K = 0: one tree force per step), dt_n = dt_h         -> T_tree per step
+    T_hard = (T_hybrid - T_soft) / (n - 1); R_hybrid = T_hybrid / (n T_tree), which is Eq. 16's
+    ((n-1) T_hard + T_soft) / (n T_tree) with the measured times (no domain decomposition on one GPU).
+    The hard force alone (walk + near pairs of a hard step) is compared with the normal tree's force (walk +
+    pairs) from a separate pass with every stage bracketed. Energy drift of the hybrid and the normal run over
+    the same simulated time (dt_h = dt_n, as the paper sets them), for N <= ENERGY_MAX_N."""
+    import numpy as np
+    import torch
+    from paper_1406_6158_gb300 import build as cuda_build
+    from paper_1406_6158_gb300 import hybrid, ics
+    cuda_build.build()
+    sizes = [args.n] if args.n != N_DEFAULT else [1 << 18, 1 << 20, 1 << 22]
+    stream = torch.cuda.Stream()           # a stream of its own: the library replays captured CUDA graphs on it
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    K = max(4, min(args.steps, 32))
+    rows, clocks = [], ClockSampler(0)
+    clocks.start()
+    for n in sizes:
+        pp = paper_params(n)
+        st = ics.plummer(n, 4)
+        forms = {
+            "hybrid": dict(R1=pp["R1"], R2=pp["R2"], n_hard=pp["n_hard"], dt_soft=pp["n_hard"] * pp["dt_h"], k=K),
+            "soft": dict(R1=pp["R1"], R2=pp["R2"], n_hard=1, dt_soft=pp["dt_h"], k=K),
+            "normal": dict(R1=0.0, R2=0.0, n_hard=1, dt_soft=pp["dt_h"], k=pp["n_hard"] * K),
+        }
+        res = {}
+        for name, f in forms.items():
+            P = hybrid.Params(eps=pp["eps"], R1=f["R1"], R2=f["R2"], dt_soft=f["dt_soft"], n_hard=f["n_hard"],
+                              a_err=pp["a_err"], mac=1, n_leaf=16, n_crit=64, precision=1)
+            ctx = hybrid.Context(P, stream)
+            s = hybrid.System(st, precision=1, ids=False)
+            chosen, _ = ctx.hybrid_autotune(s)
+            ctx.hybrid_step(s, 0)
+            # direct FP64 summation on the device is O(N^2) on GB300's FP64 pipe: small systems only
+            with_energy = name != "soft" and n <= ENERGY_MAX_N
+            e0 = sum(ctx.hybrid_energy(s)) if with_energy else None
+            for _ in range(3):
+                ctx.hybrid_step(s, 1)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(f["k"])]
+            torch.cuda.synchronize()
+            for k in range(f["k"]):
+                flush.zero_()
+                ev[k][0].record(stream)
+                ctx.hybrid_step(s, 1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            t = sum(a.elapsed_time(b) for a, b in ev) / 1e3 / f["k"]
+            e1 = sum(ctx.hybrid_energy(s)) if with_energy else None
+            kp = min(f["k"], 16)
+            ctx.hybrid_profile(2)
+            ctx.hybrid_profile_read(0, reset=True)
+            for _ in range(kp):
+                ctx.hybrid_step(s, 1)
+            torch.cuda.synchronize()
+            kinds = [ctx.hybrid_profile_read(k)[0] / kp / 1e3 for k in range(5)]   # far, near, walk, tree, kick
+            ctx.hybrid_profile(0)
+            res[name] = dict(t=t, force=kinds[0] + kinds[1] + kinds[2], tree=kinds[3],
+                             drift=abs(e1 - e0) / abs(e0) if with_energy else None, steps=3 + f["k"], tuned=list(chosen))
+            if name == "hybrid":
+                out = s.numpy()
+                a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+                a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+                res[name]["ferr"] = force_error_rms(out, a_s, a_h, pp["eps"], nsample=256)
+            ctx.close()
+        nh = pp["n_hard"]
+        T_hyb, T_soft, T_tree = res["hybrid"]["t"], res["soft"]["t"], res["normal"]["t"]
+        T_hard = (T_hyb - T_soft) / (nh - 1)
+        hard_force = (res["hybrid"]["force"] - res["soft"]["force"]) / (nh - 1)
+        rows.append({
+            "N": n, "eps": pp["eps"], "dt_h": pp["dt_h"], "R1": pp["R1"], "R2": pp["R2"],
+            "ms": {"T_hybrid_per_dt_s": 1e3 * T_hyb, "T_soft": 1e3 * T_soft, "T_hard": 1e3 * T_hard,
+                   "T_tree": 1e3 * T_tree, "hard_force": 1e3 * hard_force, "normal_force": 1e3 * res["normal"]["force"]},
+            "T_hard_over_T_soft": T_hard / T_soft,
+            "T_hard_over_T_tree": T_hard / T_tree,
+            "T_soft_over_T_tree": T_soft / T_tree,
+            "hard_force_over_normal_force": hard_force / res["normal"]["force"],
+            "R_hybrid": T_hyb / (nh * T_tree),
+            "energy_drift": {"hybrid": res["hybrid"]["drift"], "normal": res["normal"]["drift"],
+                             "hybrid_soft_steps": res["hybrid"]["steps"], "normal_steps": res["normal"]["steps"]},
+            "force_err_rms_vs_direct": res["hybrid"]["ferr"],
+            "particle_steps_per_s": {"hybrid": n / T_hyb, "normal": n / (nh * T_tree)},
+            "autotuned": {k: v["tuned"] for k, v in res.items()},
+        })
+    clk = clocks.stop()
+    head = rows[len(rows) // 2]
+    line = {
+        "metric": METRIC, "value": head["particle_steps_per_s"]["hybrid"], "unit": METRIC, "n_gpus": 1,
+        "steps": K, "warmup": 3, "ms_per_step": head["ms"]["T_hybrid_per_dt_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "Plummer sphere seed 4 with the paper's parameters: eps=0.1N^-0.26, dt_h=eps/0.65, "
+                               "n=4, R1=1.03N^-1/3, R2=2R1, absolute MAC a_err=2^-8; FP32 pairs, FP64 state; "
+                               "value at N=%d" % head["N"],
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "paper_comparison": rows,
+        "paper_values": {"T_hard_over_T_soft": "about 0.6 (Sec. IV-C, 32M particles, many GPUs)",
+                         "hard_force_over_normal_force": "about 0.4 (Sec. IV-B, N 256k-4096k)",
+                         "R_hybrid": "0.8-0.9 measured, 0.7 from Eq. 16 with its assumptions (Sec. IV-D)"},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,9 +619,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large", "paper"],
                     help="single: one Plummer sphere (default); batched: the 512-system ensemble; "
-                         "served: the Poisson request stream; large: the 2^24 Hernquist sphere")
+                         "served: the Poisson request stream; large: the 2^24 Hernquist sphere; "
+                         "paper: hybrid against normal tree with the paper's parameters")
     ap.add_argument("--tune", default="auto",
                     help="auto (autotuner) or n_crit,threads_per_group,tile_depth for the single workload")
     ap.add_argument("--c4-count", type=int, default=512)
@@ -517,6 +638,8 @@ def main():
         return run_c5(args)
     if args.workload == "large" and args.impl == "gb300":
         return run_c3(args)
+    if args.workload == "paper" and args.impl == "gb300":
+        return run_paper(args)
     if args.impl == "reference":
         return run_reference(args, w)
     args.warmup = max(args.warmup, 3)

@@ -27,6 +27,7 @@ constexpr int SCAN_SEG = SCAN_THREADS * SCAN_IPT; // 2048 elements per scan segm
 struct SysParams {
     double G, eps2, theta, R1, R2, dt_soft, a_err;
     double R2sq, invdR;            // R2^2, 1/(R2-R1) (0 when there is no hard part)
+    double h_soft, dt_hard, h_hard;   // dt_soft/2, dt_soft/n_hard, dt_hard/2 (each correctly rounded)
     float Gf, eps2f, R2f, R2sqf, invdRf, R2sqlo;   // R2sqf + R2sqlo = R2^2 to ~2^-48
     int32_t mac, has_hard;
 };

@@ -131,6 +131,9 @@ SysParams make_sp(const hybrid_params &p)
     s.R2 = p.R2;
     s.dt_soft = p.dt_soft;
     s.a_err = p.a_err;
+    s.h_soft = 0.5 * p.dt_soft;
+    s.dt_hard = p.dt_soft / (double)p.n_hard;
+    s.h_hard = 0.5 * s.dt_hard;
     s.has_hard = p.R2 > 0.0 ? 1 : 0;
     s.R2sq = s.has_hard ? p.R2 * p.R2 : 0.0;
     s.invdR = s.has_hard ? 1.0 / (p.R2 - p.R1) : 0.0;

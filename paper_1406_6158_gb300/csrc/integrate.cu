@@ -88,22 +88,35 @@ struct KickSpec {
     double dval;
 };
 
+// Exact FP32 -> FP64 conversion of a normal number with integer operations
+// (sign, exponent rebiased by 1023 - 127, mantissa moved up 29 bits); zero keeps
+// its sign, and subnormals, infinities and NaNs take the ordinary conversion.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+    if (e == 0u || e == 0xffu) return (b & 0x7fffffffu) == 0u ? __longlong_as_double((long long)sign) : (double)f;
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
+// The step sizes of each kind are per-system constants (SysParams), so a
+// particle's update is the three products and sums per vector and nothing else.
 template <typename A>
 __global__ void __launch_bounds__(256) k_kick_drift(int64_t N, StatePtrs w, const SysParams *__restrict__ sp,
-                                                    int n_hard, KickSpec ks, const Status *st)
+                                                    KickSpec ks, const Status *st)
 {
     if (st->code) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const double dts = sp[w.psys[i]].dt_soft;
+        const SysParams &P = sp[w.psys[i]];
         double v0 = w.x[3][i], v1 = w.x[4][i], v2 = w.x[5][i];
         for (int k = 0; k < ks.n; ++k) {
-            double h = ks.val[k];
-            if (ks.mode[k] == 1) h = 0.5 * dts;
-            else if (ks.mode[k] == 2) h = 0.5 * __ddiv_rn(dts, (double)n_hard);
+            const double h = ks.mode[k] == 1 ? P.h_soft : ks.mode[k] == 2 ? P.h_hard : ks.val[k];
             void *const *acc = ks.which[k] ? w.ah : w.as;
-            const double a0 = (double)((const A *)acc[0])[i];
-            const double a1 = (double)((const A *)acc[1])[i];
-            const double a2 = (double)((const A *)acc[2])[i];
+            const double a0 = widen(((const A *)acc[0])[i]);
+            const double a1 = widen(((const A *)acc[1])[i]);
+            const double a2 = widen(((const A *)acc[2])[i]);
             v0 = __dadd_rn(v0, __dmul_rn(h, a0));
             v1 = __dadd_rn(v1, __dmul_rn(h, a1));
             v2 = __dadd_rn(v2, __dmul_rn(h, a2));
@@ -112,7 +125,7 @@ __global__ void __launch_bounds__(256) k_kick_drift(int64_t N, StatePtrs w, cons
         w.x[4][i] = v1;
         w.x[5][i] = v2;
         if (ks.dmode >= 0) {
-            const double dt = ks.dmode == 0 ? ks.dval : __ddiv_rn(dts, (double)n_hard);
+            const double dt = ks.dmode == 0 ? ks.dval : P.dt_hard;
             w.x[0][i] = __dadd_rn(w.x[0][i], __dmul_rn(dt, v0));
             w.x[1][i] = __dadd_rn(w.x[1][i], __dmul_rn(dt, v1));
             w.x[2][i] = __dadd_rn(w.x[2][i], __dmul_rn(dt, v2));
@@ -126,9 +139,9 @@ __global__ void __launch_bounds__(256) k_kick_ext(int64_t n, double *vx, double 
                                                   const A *ay, const A *az, double h)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        vx[i] = __dadd_rn(vx[i], __dmul_rn(h, (double)ax[i]));
-        vy[i] = __dadd_rn(vy[i], __dmul_rn(h, (double)ay[i]));
-        vz[i] = __dadd_rn(vz[i], __dmul_rn(h, (double)az[i]));
+        vx[i] = __dadd_rn(vx[i], __dmul_rn(h, widen(ax[i])));
+        vy[i] = __dadd_rn(vy[i], __dmul_rn(h, widen(ay[i])));
+        vz[i] = __dadd_rn(vz[i], __dmul_rn(h, widen(az[i])));
     }
 }
 
@@ -258,11 +271,11 @@ void launch_kick_seq(hybrid_ctx *c, int n, const int *which, const int *mode, co
     cudaEvent_t e0 = nullptr;
     prof_begin(c, PROF_INTEG, &e0);
     if (c->p.precision == 1)
-        k_kick_drift<float><<<grid, 256, 0, c->st>>>(N, state_ptrs(c), (const SysParams *)c->sp_dev.p, c->p.n_hard, ks,
+        k_kick_drift<float><<<grid, 256, 0, c->st>>>(N, state_ptrs(c), (const SysParams *)c->sp_dev.p, ks,
                                                       status_dev(c));
     else
-        k_kick_drift<double><<<grid, 256, 0, c->st>>>(N, state_ptrs(c), (const SysParams *)c->sp_dev.p, c->p.n_hard,
-                                                       ks, status_dev(c));
+        k_kick_drift<double><<<grid, 256, 0, c->st>>>(N, state_ptrs(c), (const SysParams *)c->sp_dev.p, ks,
+                                                       status_dev(c));
     prof_end(c, PROF_INTEG, e0);
     c->launches++;
 }
