@@ -158,8 +158,9 @@ constexpr int PER = TILE / 32;
 
 // Rebased sources: the near kernel keeps {x, y, z, m} in tile[0, TILE); the
 // far kernel keeps each source twice over, {x, x, y, y} {z, z, m, m}, for the
-// packed two-sink arithmetic, in tile[0, 2 PADT): entries from nt up to
-// PADT = TILE + 32 are zero-mass sources.
+// packed two-sink arithmetic, or in the expanded form of exp_tile, two float4
+// per entry, in tile[0, 2 PADT): entries from nt up to PADT = TILE + 32 are
+// zero-mass sources (all zero in either form).
 constexpr int PADT = TILE + 32;
 static_assert(2 * PADT >= 3 * TILE, "the near filter keeps three float4 rows of TILE entries");
 template <int NST>
@@ -194,8 +195,8 @@ struct ItemSrc {
         }
     }
     // gathers of tile t into stage t % NST; always closes one cp.async group
-    template <int NST>
-    __device__ __forceinline__ void issue(const PairArgs &a, WarpStage<NST> &S, int t, int lane,
+    template <int NST, typename Stage>
+    __device__ __forceinline__ void issue(const PairArgs &a, Stage &S, int t, int lane,
                                           const uint32_t (&idx)[PER]) const
     {
         const int st = t % NST;
@@ -220,16 +221,17 @@ struct SinkBox {
 };
 
 // Staging modes: FAR_PACKED writes every source twice over for the packed far
-// sweep and calls body(stage, nt). NEAR_FILTER keeps a source for the near
+// sweep and calls body(stage, nt); FAR_EXP writes the expanded form of
+// exp_tile and calls body(stage, nt). NEAR_FILTER keeps a source for the near
 // body only when its distance to the sinks' box is below R2 (computed like the
 // pair distance, so no pair with r < R2 is dropped): kept sources go to
 // tile[0, n_in) with their rebased hi part at tile[TILE + j] and raw lo part at
 // tile[2 TILE + j]; the others (K = 0 for every sink) to tile[TILE - n_out,
 // TILE); then body(n_in, n_out).
-enum { FAR_PACKED = 0, NEAR_FILTER = 1 };
+enum { FAR_PACKED = 0, NEAR_FILTER = 1, FAR_EXP = 2 };
 
-template <int SMODE, int NST, typename Body>
-__device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, WarpStage<NST> &S, int lane,
+template <int SMODE, int NST, typename Stage, typename Body>
+__device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, Stage &S, int lane,
                                          float crx, float cry, float crz, const SinkBox &sb, Body &&body)
 {
     static_assert(NST >= 2 && NST <= 4, "staging depth");
@@ -241,17 +243,17 @@ __device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, 
 #pragma unroll
         for (int t = 0; t < NST - 1; ++t) src.load_idx(a, t, lane, ip[t]);
 #pragma unroll
-        for (int t = 0; t < NST - 1; ++t) src.issue(a, S, t, lane, ip[t]);
+        for (int t = 0; t < NST - 1; ++t) src.issue<NST>(a, S, t, lane, ip[t]);
     }
     uint32_t i0[PER];
     src.load_idx(a, NST - 1, lane, i0);
     for (int t = 0; t < ntile; ++t) {
-        src.issue(a, S, t + NST - 1, lane, i0);   // no copies past the end, but one group per tile
+        src.issue<NST>(a, S, t + NST - 1, lane, i0);   // no copies past the end, but one group per tile
         if (t + NST < ntile) src.load_idx(a, t + NST, lane, i0);
         cp_wait<NST - 1>();                       // this lane's copies of tile t have landed
         const int st = t % NST;
         const int nt = (int)min((uint32_t)TILE, ne - (uint32_t)(t * TILE));
-        if (SMODE == FAR_PACKED) {
+        if (SMODE == FAR_PACKED || SMODE == FAR_EXP) {
 #pragma unroll
             for (int u = 0; u < PER; ++u) {   // entries past nt become zero-mass sources
                 const int el = u * 32 + lane;
@@ -260,8 +262,14 @@ __device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, 
                     const float4 h = S.rh[st][el], l = S.rl[st][el];
                     v = make_float4((h.x - crx) + l.x, (h.y - cry) + l.y, (h.z - crz) + l.z, h.w);
                 }
-                S.tile[2 * el] = make_float4(v.x, v.x, v.y, v.y);
-                S.tile[2 * el + 1] = make_float4(v.z, v.z, v.w, v.w);
+                if (SMODE == FAR_PACKED) {
+                    S.tile[2 * el] = make_float4(v.x, v.x, v.y, v.y);
+                    S.tile[2 * el + 1] = make_float4(v.z, v.z, v.w, v.w);
+                } else {
+                    const float c = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+                    S.tile[2 * el] = make_float4(-2.0f * v.x, -2.0f * v.y, -2.0f * v.z, c);
+                    S.tile[2 * el + 1] = make_float4(v.w * v.x, v.w * v.y, v.w * v.z, v.w);
+                }
             }
             __syncwarp();
             body(st, nt);
@@ -358,6 +366,13 @@ __device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
     return d;
 }
 
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.ftz.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // the body of body_far for two sinks (S*) against one source given twice
 // over (X2 = {x, x}, ..): the same roundings per lane
 template <bool GUARD>
@@ -384,8 +399,8 @@ __device__ __forceinline__ void body_far2(uint64_t X2, uint64_t Y2, uint64_t Z2,
 // lane runs the same number of rounds of two sources (entries from nt to
 // PADT are zero-mass sources), so the loop has no divergence; lanes outside
 // the copies compute sums that are never used. KP sink pairs per lane.
-template <int KP, bool GUARD, int NST>
-__device__ __forceinline__ void far_tile(const WarpStage<NST> &S, int nt, int copy, int copies, uint64_t E2,
+template <int KP, bool GUARD, typename Stage>
+__device__ __forceinline__ void far_tile(const Stage &S, int nt, int copy, int copies, uint64_t E2,
                                          const uint64_t (&SX)[KP], const uint64_t (&SY)[KP], const uint64_t (&SZ)[KP],
                                          uint64_t (&AX)[KP], uint64_t (&AY)[KP], uint64_t (&AZ)[KP])
 {
@@ -406,15 +421,70 @@ __device__ __forceinline__ void far_tile(const WarpStage<NST> &S, int nt, int co
     }
 }
 
+// Far sources in expanded form. With the source at s and a sink at k
+// (both group-relative), r^2 = |s|^2 + (|k|^2 + eps^2) - 2 s.k and
+// sum_j m_j r_j^-3 (s_j - k) = sum_j r_j^-3 (m_j s_j) - k sum_j r_j^-3 m_j, so
+// a source stages {-2s, |s|^2, m s, m} and a pair costs the sum c + Q, three
+// fma for r^2, rsqrt, two mul for r^-3 and four fma: 10 FP32 lane operations
+// against 12 for body_far. The walk takes a cell only beyond its opening
+// radius and beyond R2 + b_max, and a far particle only beyond R2 of the
+// sinks' box, so r is not small against |s| and |k| and the cancellation in
+// r^2 stays a few units of FP32 rounding. Without a hard part a sink meets its
+// neighbours among the far particles: those items keep body_far.
+// Q = |k|^2 + eps^2 per sink; the caller subtracts k FM from A at the end.
+__device__ __forceinline__ void body_exp2(uint64_t NX, uint64_t NY, uint64_t NZ, uint64_t C2, uint64_t MX, uint64_t MY,
+                                           uint64_t MZ, uint64_t M2, uint64_t SX, uint64_t SY, uint64_t SZ, uint64_t Q,
+                                           uint64_t &AX, uint64_t &AY, uint64_t &AZ, uint64_t &FM)
+{
+    const uint64_t r2 = fma2(NX, SX, fma2(NY, SY, fma2(NZ, SZ, add2(C2, Q))));
+    float ra, rb;
+    upk2(r2, ra, rb);
+    const uint64_t ri = pk2(rsqrtf(ra), rsqrtf(rb));
+    const uint64_t t = mul2(mul2(ri, ri), ri);
+    AX = fma2(MX, t, AX);
+    AY = fma2(MY, t, AY);
+    AZ = fma2(MZ, t, AZ);
+    FM = fma2(M2, t, FM);
+}
+
+// The expanded sweep of one tile (same rounds and copies as far_tile); each
+// source is stored once, {-2s, |s|^2} {m s, m}, and every value is paired
+// with itself in registers for the packed arithmetic.
+template <int KP, typename Stage>
+__device__ __forceinline__ void exp_tile(const Stage &S, int nt, int copy, int copies, const uint64_t (&SX)[KP],
+                                          const uint64_t (&SY)[KP], const uint64_t (&SZ)[KP], const uint64_t (&Q)[KP],
+                                          uint64_t (&AX)[KP], uint64_t (&AY)[KP], uint64_t (&AZ)[KP],
+                                          uint64_t (&FM)[KP])
+{
+    const int rounds = (nt + 2 * copies - 1) / (2 * copies);
+    uint32_t q = (uint32_t)__cvta_generic_to_shared(S.tile) + 32u * (uint32_t)copy;
+    const uint32_t step = 32u * (uint32_t)copies;
+    for (int m = 0; m < rounds; ++m, q += 2 * step) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t qa = q + (h ? step : 0u);
+            float nx, ny, nz, c, mx, my, mz, ms;
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(nx), "=f"(ny), "=f"(nz), "=f"(c) : "r"(qa));
+            asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(mx), "=f"(my), "=f"(mz), "=f"(ms) : "r"(qa + 16));
+            const uint64_t NX = pk2(nx, nx), NY = pk2(ny, ny), NZ = pk2(nz, nz), C2 = pk2(c, c);
+            const uint64_t MX = pk2(mx, mx), MY = pk2(my, my), MZ = pk2(mz, mz), M2 = pk2(ms, ms);
+#pragma unroll
+            for (int k = 0; k < KP; ++k)
+                body_exp2(NX, NY, NZ, C2, MX, MY, MZ, M2, SX[k], SY[k], SZ[k], Q[k], AX[k], AY[k], AZ[k], FM[k]);
+        }
+    }
+}
+
 // NEAR = false: cells + far particles -> soft. NEAR = true: near particles ->
 // soft (1 - K) and/or hard (K), by SOFT/HARD.
 template <int KS, bool NEAR, bool SOFT, bool HARD, int NST>
 __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
 {
-    __shared__ WarpStage<NST> stages[PAIR_WARPS];
+    using Stage = WarpStage<NST>;
+    __shared__ Stage stages[PAIR_WARPS];
     if (a.st->code) return;
     const int lane = threadIdx.x & 31;
-    WarpStage<NST> &S = stages[threadIdx.x >> 5];
+    Stage &S = stages[threadIdx.x >> 5];
     for (int e = 2 * TILE + lane; e < 2 * PADT; e += 32) S.tile[e] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     const int64_t W = (int64_t)*a.nwork;
     unsigned long long inter = 0;
@@ -473,14 +543,37 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                     AX[p] = AY[p] = AZ[p] = 0ull;
                 }
                 const uint64_t E2 = pk2(H.eps2, H.eps2);
-                if (H.eps2 > 0.0f)
-                    pipeline<FAR_PACKED>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
-                        far_tile<KP, false, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                // the expanded form: cells always; far particles when there is a hard part (then every
+                // far particle is at least R2 from the sinks' box; without one, a sink meets its neighbours)
+                if (H.eps2 > 0.0f && (d.e1 <= d.Lc || P.has_hard)) {
+                    uint64_t Q[KP], FM[KP];
+#pragma unroll
+                    for (int p = 0; p < KP; ++p) {
+                        const int k1 = 2 * p + 1 < KS ? 2 * p + 1 : 2 * p;
+                        Q[p] = pk2(fmaf(sx[2 * p], sx[2 * p], fmaf(sy[2 * p], sy[2 * p], fmaf(sz[2 * p], sz[2 * p], H.eps2))),
+                                   fmaf(sx[k1], sx[k1], fmaf(sy[k1], sy[k1], fmaf(sz[k1], sz[k1], H.eps2))));
+                        FM[p] = 0ull;
+                    }
+                    pipeline<FAR_EXP, NST>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
+                        exp_tile<KP>(S, nt, copy, copies, SX, SY, SZ, Q, AX, AY, AZ, FM);
                     });
-                else   // eps = 0 without a hard part: a sink meets itself in its far particles
-                    pipeline<FAR_PACKED>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
-                        far_tile<KP, true, NST>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
-                    });
+#pragma unroll
+                    for (int p = 0; p < KP; ++p) {   // A - k FM
+                        const int k1 = 2 * p + 1 < KS ? 2 * p + 1 : 2 * p;
+                        AX[p] = fma2(pk2(-sx[2 * p], -sx[k1]), FM[p], AX[p]);
+                        AY[p] = fma2(pk2(-sy[2 * p], -sy[k1]), FM[p], AY[p]);
+                        AZ[p] = fma2(pk2(-sz[2 * p], -sz[k1]), FM[p], AZ[p]);
+                    }
+                } else {
+                    if (H.eps2 > 0.0f)
+                        pipeline<FAR_PACKED, NST>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
+                            far_tile<KP, false>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                        });
+                    else   // eps = 0 without a hard part: a sink meets itself in its far particles
+                        pipeline<FAR_PACKED, NST>(a, src, S, lane, crx, cry, crz, SinkBox(), [&](int, int nt) {
+                            far_tile<KP, true>(S, nt, copy, copies, E2, SX, SY, SZ, AX, AY, AZ);
+                        });
+                }
 #pragma unroll
                 for (int p = 0; p < KP; ++p) {
                     float t0, t1;
@@ -525,7 +618,7 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                     sb.hi[1] = hi1;
                     sb.hi[2] = hi2;
                 }
-                pipeline<NEAR_FILTER>(a, src, S, lane, crx, cry, crz, sb, [&](int n_in, int n_out) {
+                pipeline<NEAR_FILTER, NST>(a, src, S, lane, crx, cry, crz, sb, [&](int n_in, int n_out) {
                     if (!active) return;
                     for (int j = copy; j < n_in; j += copies) {   // sources within R2 of the box
                         const float4 q = S.tile[j];
