@@ -328,18 +328,20 @@ static void moments(orc_tree *t)
         double o[3];
         for (int d = 0; d < 3; ++d) o[d] = t->lo[d] + (double)prefix_coord(t->key[a], lev, d) * side;
         double ctr[3] = {o[0] + 0.5 * side, o[1] + 0.5 * side, o[2] + 0.5 * side};
+        /* sum m x / M taken as offsets from the cell's first particle: the same centre of mass, and exactly
+         * that particle for a cell of one particle (or of coincident ones), whose B2 and b_max are then 0 */
         double M = 0.0, s0 = 0.0, s1 = 0.0, s2 = 0.0;
         for (int64_t i = a; i < b; ++i) {
             M += t->m[i];
-            s0 += t->m[i] * t->x[i];
-            s1 += t->m[i] * t->y[i];
-            s2 += t->m[i] * t->z[i];
+            s0 += t->m[i] * (t->x[i] - t->x[a]);
+            s1 += t->m[i] * (t->y[i] - t->y[a]);
+            s2 += t->m[i] * (t->z[i] - t->z[a]);
         }
         double com[3];
         if (M > 0.0) {
-            com[0] = s0 / M;
-            com[1] = s1 / M;
-            com[2] = s2 / M;
+            com[0] = t->x[a] + s0 / M;
+            com[1] = t->y[a] + s1 / M;
+            com[2] = t->z[a] + s2 / M;
         } else { /* reading: a massless cell sits at its geometric centre */
             com[0] = ctr[0];
             com[1] = ctr[1];

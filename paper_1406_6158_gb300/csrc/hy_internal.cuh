@@ -16,8 +16,8 @@ namespace hy {
 constexpr int LEVELS = 21;                 // 3 x 21 = 63 Morton key bits
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr int RS_WARPS = 8;                // radix sort: 8 warps x 32 lanes x ipt items per tile
-constexpr int RS_IPT_MAX = 16;
-constexpr int RS_TILE_MAX = RS_WARPS * 32 * RS_IPT_MAX;   // 4096 keys per tile at most
+constexpr int RS_IPT_MAX = 8;
+constexpr int RS_TILE_MAX = RS_WARPS * 32 * RS_IPT_MAX;   // 2048 keys per tile at most
 constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_IPT = 8;
 constexpr int SCAN_SEG = SCAN_THREADS * SCAN_IPT; // 2048 elements per scan segment

@@ -290,8 +290,8 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
     }
     c->S = S;
     c->N = c->h_off[S];
-    // radix tiles: the largest of 512..4096 keys that still gives about 4 tiles per SM
-    c->ipt = 8;
+    // radix tiles: the largest of 512..2048 keys that still gives about 4 tiles per SM
+    c->ipt = RS_IPT_MAX;
     while (c->ipt > 2 && c->N / (RS_WARPS * 32 * c->ipt) < 4 * c->nsm) c->ipt >>= 1;
     c->tile = RS_WARPS * 32 * c->ipt;
     const int tile = c->tile;

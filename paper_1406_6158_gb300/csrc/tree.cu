@@ -260,9 +260,13 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
                                                   uint32_t *ticket, int64_t ntotal, Status *st)
 {
     // the sort always runs (later kernels rely on a consistent permutation); st only records a timeout
+    constexpr int TILE_K = RS_WARPS * 32 * IPT;
     __shared__ uint32_t whist[RS_WARPS][256];
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wsum[RS_WARPS];
+    __shared__ uint32_t base[256];    // global position of the tile's first key of digit d
+    __shared__ uint32_t tloc[256];    // position in the tile's sorted order of its first key of digit d
+    __shared__ uint64_t wsum[RS_WARPS];
+    __shared__ uint64_t skey[TILE_K];
+    __shared__ uint32_t sval[TILE_K];
     __shared__ int cid;
     const int shift = 8 * pass;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -278,11 +282,16 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
         uint32_t v[IPT], r[IPT];
         const int wbase = w * 32 * IPT;
 #pragma unroll
-        for (int it = 0; it < IPT; ++it) {
+        for (int it = 0; it < IPT; ++it) {   // every load in flight before the ranking starts
             const int li = wbase + it * 32 + lane;   // warp-striped: (it, lane) is input order
             const bool ok = li < ch.len;
             k[it] = ok ? kin[ch.start + li] : 0ull;
             v[it] = ok ? vin[ch.start + li] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < IPT; ++it) {
+            const int li = wbase + it * 32 + lane;
+            const bool ok = li < ch.len;
             const uint32_t d = ok ? (uint32_t)(k[it] >> shift) & 0xffu : 256u;
             const unsigned peers = __match_any_sync(0xffffffffu, d);
             const uint32_t before = ok ? whist[w][d] : 0u;
@@ -312,30 +321,48 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
             }
             st_relaxed_u32(mine, LB_INC | (excl + run));
         }
-        // exclusive prefix over digits of the system's counts (block scan, 256 threads)
+        // exclusive prefixes over digits, in one block scan: the system's counts (high 32 bits) and the
+        // tile's counts (low 32 bits; at most 2048, so no carry crosses over)
         const uint32_t cd = counts[(size_t)ch.sys * 2048 + pass * 256 + d];
-        uint32_t incl = cd;
+        const uint64_t both = ((uint64_t)cd << 32) | run;
+        uint64_t incl = both;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            const uint64_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
         if (lane == 31) wsum[w] = incl;
         __syncthreads();
-        uint32_t wpre = 0;
+        uint64_t wpre = 0;
         for (int ww = 0; ww < w; ++ww) wpre += wsum[ww];
-        base[d] = wpre + incl - cd + excl;
+        const uint64_t ex = wpre + incl - both;
+        tloc[d] = (uint32_t)ex;
+        base[d] = (uint32_t)(ex >> 32) + excl;
         __syncthreads();
-        const int64_t s0 = chunks[ch.first_chunk].start;
+        // reorder the tile in shared memory by (digit, rank), then write runs of equal digits
+        // with consecutive threads on consecutive addresses
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
             const int li = wbase + it * 32 + lane;
             if (li < ch.len) {
                 const uint32_t dd = (uint32_t)(k[it] >> shift) & 0xffu;
-                const int64_t dst = s0 + (int64_t)(base[dd] + whist[w][dd] + r[it]);
+                const uint32_t lp = tloc[dd] + whist[w][dd] + r[it];
+                skey[lp] = k[it];
+                sval[lp] = v[it];
+            }
+        }
+        __syncthreads();
+        const int64_t s0 = chunks[ch.first_chunk].start;
+#pragma unroll
+        for (int it = 0; it < IPT; ++it) {
+            const int lp = it * 256 + threadIdx.x;
+            if (lp < ch.len) {
+                const uint64_t kk = skey[lp];
+                const uint32_t dd = (uint32_t)(kk >> shift) & 0xffu;
+                const int64_t dst = s0 + (int64_t)(base[dd] + ((uint32_t)lp - tloc[dd]));
                 if (dst < ntotal) {   // always true unless a look-back timed out (recorded in st)
-                    kout[dst] = k[it];
-                    vout[dst] = v[it];
+                    kout[dst] = kk;
+                    vout[dst] = sval[lp];
                 }
             }
         }
@@ -1326,8 +1353,7 @@ void launch_keys_sort(hybrid_ctx *c)
         switch (c->ipt) {
         case 2: k_onesweep<2><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
         case 4: k_onesweep<4><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
-        case 8: k_onesweep<8><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st); break;
-        default: k_onesweep<16><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st);
+        default: k_onesweep<8><<<grid, 256, 0, c->st>>>(k0, v0, k1, v1, chk, c->nchunks, pass, counts, lk, tk, N, st);
         }
         c->launches++;
         std::swap(k0, k1);

@@ -56,6 +56,12 @@ CASES = [
     ("hernquist20000", lambda: ics.hernquist(20000, 2), dict(theta=0.4, eps=1 / 512)),
     ("leaf1_capacity", lambda: ics.plummer(6000, 5), dict(n_leaf=1, n_crit=16)),
 ]
+# the absolute MAC (Eq. 5) with the paper's a_err, and the normal tree (R1 = R2 = 0: K = 0, no hard part)
+MODE_CASES = [
+    ("absmac8000", lambda: ics.plummer(8000, 11), dict(mac=1, a_err=2.0 ** -8)),
+    ("normal6000", lambda: ics.plummer(6000, 12), dict(R1=0.0, R2=0.0)),
+    ("normal_absmac6000", lambda: ics.plummer(6000, 13), dict(R1=0.0, R2=0.0, mac=1, a_err=2.0 ** -8)),
+]
 
 
 def coincident_state():
@@ -102,11 +108,24 @@ def check_tree(T, G, prec):
         rtol = 4e-6
     fin = np.isfinite(mo["rb"])
     assert np.array_equal(np.isfinite(gm[:, 11]), fin)
-    assert np.all(np.abs(gm[fin, 11] - mo["rb"][fin]) <= rtol * (mo["rb"][fin] + side[fin]))
+    if T.params.mac == 1:
+        # Eq. (5): r_b = b/2 + sqrt(b^2/4 + sqrt(3 B2 / a_err)) is monotone in b_max and B2, so the tolerances
+        # held above for b_max and B2 bound it (the fourth root magnifies small B2's errors)
+        tb = (1e-12 if prec == 0 else 2e-6) * mo["bmax"] + (1e-12 if prec == 0 else 4e-6) * scale
+        tB = (1e-12 if prec == 0 else 1e-5) * mo["B2"] + (1e-12 if prec == 0 else 1e-10) * mo["M"] * side ** 2
+
+        def rb(b, B2):
+            return 0.5 * b + np.sqrt(0.25 * b * b + np.sqrt(3.0 * np.maximum(B2, 0.0) / T.params.a_err))
+        lo = rb(np.maximum(mo["bmax"] - tb, 0.0), mo["B2"] - tB)
+        hi = rb(mo["bmax"] + tb, mo["B2"] + tB)
+        slack = rtol * side
+        assert np.all(gm[fin, 11] >= lo[fin] - slack[fin]) and np.all(gm[fin, 11] <= hi[fin] + slack[fin])
+    else:
+        assert np.all(np.abs(gm[fin, 11] - mo["rb"][fin]) <= rtol * (mo["rb"][fin] + side[fin]))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("name,mk,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("name,mk,kw", CASES + MODE_CASES[:1], ids=[c[0] for c in CASES + MODE_CASES[:1]])
 def test_tree_bit_exact(H, name, mk, kw, prec):
     st = mk()
     P = plummer_params(len(st["x"]), prec, **kw)
@@ -117,6 +136,26 @@ def test_tree_bit_exact(H, name, mk, kw, prec):
     assert np.array_equal(out["x"], T.x) and np.array_equal(out["m"], T.m)
     assert np.array_equal(ctx.hybrid_get_perm(T.n).cpu().numpy(), T.perm)
     check_tree(T, G, prec)
+
+
+@pytest.mark.parametrize("sizes", [[1 << 21], [700001], [300000, 5, 1 << 20, 77777]],
+                         ids=["2M_tiles2048", "700k_tiles1024", "batched_ragged"])
+def test_sort_order_large(H, sizes):
+    # The radix tile grows with N (512, 1024, 2048 keys): at every tile size the order is the stable order of
+    # the oracle's Morton keys, and systems that share the digit passes do not mix.
+    states = [ics.plummer(n, 20 + k) for k, n in enumerate(sizes)]
+    P = plummer_params(max(sizes), 1, eps=1 / 256)
+    ctx = H.Context(P)
+    systems = [H.System(st, precision=1) for st in states]
+    if len(systems) == 1:
+        ctx.hybrid_build_tree(systems[0])
+    else:
+        ctx.hybrid_step_batched(systems, 0)
+    torch.cuda.synchronize()
+    for st, s in zip(states, systems):
+        lo, L = oracle.root_box(st["x"], st["y"], st["z"])
+        perm = oracle.stable_sort(oracle.morton_keys(st["x"], st["y"], st["z"], lo, L))
+        assert np.array_equal(s.numpy()["id"], perm)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 33])
@@ -179,7 +218,7 @@ def lists_match(T, gl, ol):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("name,mk,kw", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("name,mk,kw", CASES[:3] + MODE_CASES, ids=[c[0] for c in CASES[:3] + MODE_CASES])
 def test_lists_and_forces(H, name, mk, kw, prec):
     st = mk()
     P = plummer_params(len(st["x"]), prec, **kw)
@@ -209,8 +248,9 @@ def test_lists_and_forces(H, name, mk, kw, prec):
         es = np.linalg.norm(g_s - a_s, axis=1) / np.linalg.norm(a_s, axis=1)
         assert np.percentile(es, 99) <= 1e-5, np.percentile(es, 99)
         nz = np.linalg.norm(a_h, axis=1) > 0
-        eh = np.linalg.norm(g_h - a_h, axis=1)[nz] / np.linalg.norm(a_h, axis=1)[nz]
-        assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
+        if nz.any():
+            eh = np.linalg.norm(g_h - a_h, axis=1)[nz] / np.linalg.norm(a_h, axis=1)[nz]
+            assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
         assert np.all(np.linalg.norm(g_h, axis=1)[~nz] == 0.0)
     far, near = ctx.hybrid_interactions()   # the last evaluation was the soft force
     os_, oh = T.interactions(mode=3)
@@ -285,10 +325,12 @@ def test_c1_trajectory_fp64(H):
     assert np.allclose(np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1), a_s, rtol=0, atol=1e-9)
 
 
-def test_step_fp32_close_to_oracle(H):
+@pytest.mark.parametrize("kw", [dict(n_hard=4), dict(n_hard=1, R1=0.0, R2=0.0, mac=1, a_err=2.0 ** -8)],
+                         ids=["hybrid", "normal_absmac"])
+def test_step_fp32_close_to_oracle(H, kw):
     st = ics.plummer(2048, 8)
     st["id"] = np.arange(2048, dtype=np.int64)
-    P = plummer_params(2048, 1, dt_soft=1 / 128, n_hard=4)
+    P = plummer_params(2048, 1, dt_soft=1 / 128, **kw)
     ctx = H.Context(P)
     s = H.System(st, precision=1)
     ctx.hybrid_step(s, 2)
@@ -387,11 +429,14 @@ def test_graph_replay_equals_eager(H, prec):
         ctx.close()
     a, b = runs
     assert np.array_equal(a["id"], b["id"])
+    # FP32 form: groups with several work items add their partial sums with atomics, in an order that differs
+    # between runs, so accelerations agree to FP32 rounding of those sums (~1e-6 relative); three soft steps of
+    # dt_s = 1/128 carry that into v and x at well below 1e-7
     for k in ("x", "y", "z", "vx", "vy", "vz"):
         if prec == 0:
             assert np.array_equal(a[k], b[k]), k
         else:
-            assert np.max(np.abs(a[k] - b[k])) <= 1e-9 * max(1.0, np.max(np.abs(a[k]))), k
+            assert np.max(np.abs(a[k] - b[k])) <= 1e-7 * max(1.0, np.max(np.abs(a[k]))), k
 
 
 def test_bounded_wait_times_out_and_context_survives(H):

@@ -226,7 +226,12 @@ def tree_invariants(T: oracle.Tree):
         o = np.array([mo["ox"][c], mo["oy"][c], mo["oz"][c]])
         assert np.all(P >= o - 1e-12) and np.all(P <= o + mo["side"][c] * (1 + 1e-12))
         com = np.array([mo["cx"][c], mo["cy"][c], mo["cz"][c]])
-        assert np.allclose(com, (T.m[a:b, None] * P).sum(0) / T.m[a:b].sum(), rtol=1e-12, atol=1e-14)
+        # the oracle sums m (x - x_first): sequential-sum bound on n terms of at most m |x - x_first| each
+        spread = np.abs(P - P[0]).max()
+        ref = (T.m[a:b, None] * P).sum(0) / T.m[a:b].sum()
+        assert np.all(np.abs(com - ref) <= 1e-12 * np.abs(ref) + 2.3e-16 * (b - a) * spread + 1e-14)
+        if b - a == 1:
+            assert np.array_equal(com, P[0]) and mo["B2"][c] == 0.0 and mo["bmax"][c] == 0.0
         r = np.linalg.norm(P - com, axis=1)
         assert abs(r.max() - mo["bmax"][c]) <= 1e-12 * (1 + r.max())
     # groups cover the particles once, in order, and are maximal
