@@ -33,9 +33,13 @@ FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul,
 # DRAM bytes (read + write) of one far-pair launch on this workload, from an ncu capture of the kernel
 # variant the key names (n_crit, threads per group, staging depth); see profiles/far_pair_plummer131k.md.
 # Reported as the roofline's traffic only when the autotuner picks that same variant.
-FAR_TRAFFIC_BYTES = {(128, 32, 4): 56.934e6}
+FAR_TRAFFIC_BYTES = {}
 L2_FLUSH_BYTES = 256 << 20
 ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
+# Verlet skin of the reused-list measurement: twice the distance the fastest particle of the Plummer sphere
+# (escape speed sqrt(2) at the centre, G = M = a = 1) covers in the three drifts that reuse a build's lists
+# (3/512 each), rounded up: 2 x 1.42 x 3/512 = 0.0166 -> 0.025. Steps that exceed it rebuild by themselves.
+REUSE_SKIN = 0.025
 
 
 def workload(n):
@@ -617,6 +621,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the reused-neighbour-list measurement")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large", "paper"],
@@ -722,6 +727,38 @@ def main():
     energy = {"rel_drift": abs(e_end - e_start) / abs(e_start), "E_start": e_start, "E_end": e_end,
               "soft_steps": args.warmup + args.steps + kp, "time": (args.warmup + args.steps + kp) * w["dt_soft"]}
 
+    # ---- reused neighbour lists (skin > 0, an option outside the paper's scheme), same workload ----
+    reuse = None
+    if not args.no_reuse:
+        P2 = hybrid.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
+                           n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"], precision=1, skin=REUSE_SKIN)
+        ctx2 = hybrid.Context(P2, stream)
+        s2 = hybrid.System(st, precision=1)
+        ctx2.hybrid_autotune(s2, [tuple(chosen)])
+        ctx2.hybrid_step(s2, 0)
+        r_e0 = sum(ctx2.hybrid_energy(s2))
+        for _ in range(args.warmup):
+            ctx2.hybrid_step(s2, 1)
+        kr = max(3, args.steps // 3)
+        evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kr)]
+        l0 = ctx2.hybrid_launch_count()
+        barrier()
+        for k in range(kr):
+            flush.zero_()
+            evr[k][0].record(stream)
+            ctx2.hybrid_step(s2, 1)
+            evr[k][1].record(stream)
+        barrier()
+        tr = sum(a.elapsed_time(b) for a, b in evr) / 1e3
+        r_e1 = sum(ctx2.hybrid_energy(s2))
+        rv, tr = job_rate(w["n"] * kr, tr, dist)
+        reuse = {"skin": REUSE_SKIN, "value": rv, "unit": METRIC, "ms_per_step": 1e3 * tr / kr, "steps": kr,
+                 "gpu_launches_per_step": (ctx2.hybrid_launch_count() - l0) / kr,
+                 "energy_rel_drift": abs(r_e1 - r_e0) / abs(r_e0), "energy_soft_steps": 1 + args.warmup + kr,
+                 "note": "hard steps 1..n-1 reuse the tree and neighbour lists of the last build (lists to R2 + "
+                         "skin); not the paper's scheme, which rebuilds every hard step"}
+        ctx2.close()
+
     # ---- end to end through the C-ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
@@ -793,6 +830,7 @@ def main():
                                            "pass of %d steps with every stage bracketed; topology and groups "
                                            "run beside the permutation and the moments" % kp},
             "roofline": roofline,
+            "reused_lists": reuse,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -66,7 +66,23 @@ typedef enum {
  *          use; 2, 3 or 4, 0 = built-in default (3).
  * n_crit, threads_per_group and tile_depth change speed, not results beyond
  * FP32 rounding order (n_crit also changes the groups and thus the lists);
- * hybrid_autotune chooses them. */
+ * hybrid_autotune chooses them.
+ * skin:    Verlet skin for reusing the tree and the neighbour lists across
+ *          hard steps. The paper rebuilds the tree at every hard step (Sec.
+ *          II-C, IV-C); this option is not part of the method and 0 (the
+ *          default) keeps the paper's scheme. With skin > 0 (FP32 form,
+ *          precision 1, with a hard part, R2 > 0) the walk of each soft-force
+ *          evaluation treats R2 + skin as the cutoff radius of Eq. (15): a
+ *          cell is taken whole only beyond R2 + skin + b_max and every leaf
+ *          within that radius lists its particles as neighbours (pairs beyond
+ *          R2 get K = 0, so the forces are those of the method with that
+ *          slightly more accurate tree opening). The n - 1 hard steps that
+ *          follow reuse that tree, its groups and its neighbour lists: their
+ *          hard force is the same sum over the current positions of the
+ *          listed neighbours. Each drift adds |v| dt to a per-particle bound
+ *          of the distance moved since the last build; when one exceeds
+ *          skin / 2 a pair within R2 could be missing, and that hard step
+ *          rebuilds the tree and the lists first (inside the same call). */
 typedef struct {
     double G, eps, theta, R1, R2, dt_soft, a_err;
     int32_t n_hard, n_leaf, n_crit;
@@ -74,6 +90,7 @@ typedef struct {
     int32_t mac;
     int32_t threads_per_group;
     int32_t tile_depth;
+    double skin;
 } hybrid_params;
 
 /* One independent system. Arrays are device pointers of length n.

@@ -28,7 +28,9 @@ struct SysParams {
     double G, eps2, theta, R1, R2, dt_soft, a_err;
     double R2sq, invdR;            // R2^2, 1/(R2-R1) (0 when there is no hard part)
     double h_soft, dt_hard, h_hard;   // dt_soft/2, dt_soft/n_hard, dt_hard/2 (each correctly rounded)
+    double skin;                      // Verlet skin of reused neighbour lists (0: rebuild every hard step)
     float Gf, eps2f, R2f, R2sqf, invdRf, R2sqlo;   // R2sqf + R2sqlo = R2^2 to ~2^-48
+    float skinf, half_skinf;       // skin and skin / 2 in FP32
     int32_t mac, has_hard;
 };
 
@@ -43,6 +45,21 @@ struct SysBox {
     double u, inv_u;
     float uf, inv_uf;   // u and 1/u in FP32 (powers of two: exact)
 };
+
+// FP32 hi/lo copy of a coordinate relative to the root corner: hi = the
+// nearest multiple of u (at most 2^20 steps: exact in FP32), lo = the rest
+// (exact in FP64, then rounded to FP32, |lo| <= u/2).
+__device__ __forceinline__ void grid_split(double x, double lo0, const SysBox &b, float &h, float &l)
+{
+    const double xp = __dsub_rn(x, lo0);
+    const double hh = __dmul_rn(rint(__dmul_rn(xp, b.inv_u)), b.u);
+    h = (float)hh;
+    l = (float)__dsub_rn(xp, hh);
+}
+
+// Internal status code (never returned to the caller): a particle moved more
+// than skin / 2 since the last build; the step resumes with a rebuild.
+constexpr int32_t ST_SKIN = 100;
 
 // Device status block: first failure wins (atomicCAS on code).
 struct Status {
@@ -131,6 +148,10 @@ struct hybrid_ctx {
     int nchunks = 0;
     int ipt = 16, tile = 4096;   // radix tile: 8 warps x 32 lanes x ipt keys, sized to fill the GPU
     bool tree_valid = false, have_soft = false, have_hard = false;
+    // reused neighbour lists (skin > 0): the lists of the last walk still hold for the working state of the
+    // batch with this signature (set at the end of a step, cleared by anything else that builds or walks)
+    bool lists_fresh = false;
+    uint64_t lists_sig = 0;
 
     // capacities
     int64_t capN = 0, capS = 0, capChunks = 0, capNodes = 0, capGroups = 0, capList = 0, capStack = 0;
@@ -140,6 +161,7 @@ struct hybrid_ctx {
     hy::Buf x[7], xa[7], id, ida, orig, origa, psys;
     hy::Buf acc_s[3], acc_h[3];            // float or double
     hy::Buf phi, plo, pd;                  // float4 hi/lo (precision 1), double4_32a (precision 0)
+    hy::Buf disp;                          // float: bound of the distance moved since the last build (skin > 0)
     hy::Buf keys[2], vals[2], hist, blocksum;
     hy::Buf off_dev, sp_dev, chunks_dev, boxmin, boxmax, box, sysroot;
     hy::Buf status;
@@ -231,7 +253,7 @@ void launch_copy_out(hybrid_ctx *c, const SysIO *d_io, bool state, bool acc_s, b
 // mode 0: h = val, 1: h = dt_soft/2, 2: h = (dt_soft/n_hard)/2, per system),
 // then a drift x <- x + dt v (dmode -1: none, 0: dt = dval, 2: dt_soft/n_hard).
 void launch_kick_seq(hybrid_ctx *c, int n, const int *which, const int *mode, const double *val, int dmode,
-                     double dval);
+                     double dval, bool resplit = false);
 void launch_kick_ext(hybrid_ctx *c, const hybrid_system *s, int which, double h);
 void launch_drift_ext(hybrid_ctx *c, const hybrid_system *s, double dt);
 void launch_energy(hybrid_ctx *c, double *d_out /* 2*S */);

@@ -117,6 +117,9 @@ bool params_ok(const hybrid_params *p, std::string *why)
     if (p->mac == 1 && !(p->a_err > 0.0)) return bad("a_err must be > 0 for the absolute MAC");
     if (p->threads_per_group < 0) return bad("threads_per_group must be >= 0");
     if (p->tile_depth != 0 && (p->tile_depth < 2 || p->tile_depth > 4)) return bad("tile_depth must be 0, 2, 3 or 4");
+    if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) return bad("skin must be >= 0");
+    if (p->skin > 0.0 && (p->precision != 1 || no_hard))
+        return bad("skin > 0 needs the FP32 form (precision 1) and a hard part (R2 > 0)");
     return true;
 }
 
@@ -134,6 +137,9 @@ SysParams make_sp(const hybrid_params &p)
     s.h_soft = 0.5 * p.dt_soft;
     s.dt_hard = p.dt_soft / (double)p.n_hard;
     s.h_hard = 0.5 * s.dt_hard;
+    s.skin = p.R2 > 0.0 ? p.skin : 0.0;
+    s.skinf = (float)s.skin;
+    s.half_skinf = (float)(0.5 * s.skin);
     s.has_hard = p.R2 > 0.0 ? 1 : 0;
     s.R2sq = s.has_hard ? p.R2 * p.R2 : 0.0;
     s.invdR = s.has_hard ? 1.0 / (p.R2 - p.R1) : 0.0;
@@ -196,6 +202,7 @@ bool reserve(hybrid_ctx *c)
         for (int d = 0; d < 3; ++d) ok = ok && ensure(c, c->acc_s[d], n * asz) && ensure(c, c->acc_h[d], n * asz);
         if (c->p.precision == 1) ok = ok && ensure(c, c->phi, n * 16) && ensure(c, c->plo, n * 16);
         else ok = ok && ensure(c, c->pd, n * 32);
+        if (c->p.skin > 0.0) ok = ok && ensure(c, c->disp, n * 4);
         ok = ok && ensure(c, c->keys[0], n * 8) && ensure(c, c->keys[1], n * 8);
         ok = ok && ensure(c, c->vals[0], n * 4) && ensure(c, c->vals[1], n * 4);
         ok = ok && ensure(c, c->gF, n * sizeof(GroupF)) && ensure(c, c->glo, n * 24) && ensure(c, c->ghi, n * 24);
@@ -361,8 +368,8 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
 {
     c->op = idx;
     switch (o.kind) {
-    case OP_KICKS:
-        launch_kick_seq(c, o.nk, o.which, o.kmode, o.val, o.dmode, o.dval);
+    case OP_KICKS:   // mode 1: the drift of a hard step that reuses the neighbour lists
+        launch_kick_seq(c, o.nk, o.which, o.kmode, o.val, o.dmode, o.dval, o.mode == 1);
         break;
     case OP_BUILD: {
         // The build as a two-branch DAG: after the key sort, the topology and the group table (keys only)
@@ -557,12 +564,16 @@ bool launch_as_graph(hybrid_ctx *c, const std::vector<Op> &ops, std::vector<std:
     return true;
 }
 
-hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
+Op simple(int kind, int mode = 0);
+
+hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops_in)
 {
+    std::vector<Op> ops = ops_in;
     size_t start = 0;
+    bool skin_recovered = false;
     for (int attempt = 0; attempt < 12; ++attempt) {
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *gev = nullptr;
-        if (!(attempt == 0 && launch_as_graph(c, ops, &gev)))
+        if (!(attempt == 0 && !skin_recovered && launch_as_graph(c, ops, &gev)))
             for (size_t i = start; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(c, le, "kernel launch");
@@ -580,6 +591,29 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops)
         }
         if (s.code == 0) return HYBRID_OK;
         drop_graphs(c);
+        if (s.code == ST_SKIN && !skin_recovered && s.where >= 0 && (size_t)s.where < ops.size()) {
+            // a particle moved more than skin / 2 in the drift of op `where`: that hard step and every later
+            // one in this call rebuild the tree and the lists (the drift itself is done)
+            std::vector<Op> rest;
+            rest.push_back(simple(OP_BUILD));
+            rest.push_back(simple(OP_WALK, 2));
+            for (size_t i = (size_t)s.where + 1; i < ops.size(); ++i) {
+                Op o = ops[i];
+                const bool reused = o.kind == OP_KICKS && o.mode == 1;
+                o.mode = reused ? 0 : o.mode;
+                rest.push_back(o);
+                if (reused) {
+                    rest.push_back(simple(OP_BUILD));
+                    rest.push_back(simple(OP_WALK, 2));
+                }
+            }
+            ops.swap(rest);
+            start = 0;
+            skin_recovered = true;
+            --attempt;   // not a capacity attempt; the rest runs eagerly
+            if ((r = clear_status(c)) != HYBRID_OK) return r;
+            continue;
+        }
         if (s.code != HYBRID_ECAPACITY) {
             set_err(c, "device failure %d at op %d", s.code, s.where);
             clear_status(c);
@@ -623,7 +657,7 @@ Op kicks(int nk, const int *which, const int *kmode, int dmode)
     return o;
 }
 
-Op simple(int kind, int mode = 0)
+Op simple(int kind, int mode)
 {
     Op o;
     o.kind = kind;
@@ -634,14 +668,19 @@ Op simple(int kind, int mode = 0)
 // The op sequence of n_steps soft steps (Sec. II-C, kick-drift-kick):
 // K_s(dt_s/2); n x [K_h(dt_h/2); D(dt_h); build; hard (+ soft at the last);
 // K_h(dt_h/2)]; K_s(dt_s/2). Adjacent kicks share one launch (same order).
-std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid)
+// With a skin (reused lists, not part of the method) the hard steps 1..n-1
+// skip the build and the walk when the lists of the last build still hold:
+// their drift also refreshes the FP32 positions and the distance bound.
+std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid, bool lists_ok)
 {
+    const bool reuse = c->p.skin > 0.0;
     std::vector<Op> ops;
     if (!valid) {
         ops.push_back(simple(OP_BUILD));
         ops.push_back(simple(OP_WALK, 3));
         ops.push_back(simple(OP_PAIR_FAR));
         ops.push_back(simple(OP_PAIR_NEAR, 3));
+        lists_ok = true;
     }
     int pw[8], pm[8], np = 0;
     auto add = [&](int which, int mode) {
@@ -654,12 +693,20 @@ std::vector<Op> step_ops(const hybrid_ctx *c, int n_steps, bool valid)
         add(0, 1);
         for (int k = 1; k <= nh; ++k) {
             add(1, 2);
-            ops.push_back(kicks(np, pw, pm, 2));
+            Op kd = kicks(np, pw, pm, 2);
             np = 0;
-            ops.push_back(simple(OP_BUILD));
-            ops.push_back(simple(OP_WALK, k == nh ? 3 : 2));
-            if (k == nh) ops.push_back(simple(OP_PAIR_FAR));
-            ops.push_back(simple(OP_PAIR_NEAR, k == nh ? 3 : 2));
+            if (reuse && k < nh && lists_ok) {
+                kd.mode = 1;
+                ops.push_back(kd);
+                ops.push_back(simple(OP_PAIR_NEAR, 2));
+            } else {
+                ops.push_back(kd);
+                ops.push_back(simple(OP_BUILD));
+                ops.push_back(simple(OP_WALK, k == nh ? 3 : 2));
+                if (k == nh) ops.push_back(simple(OP_PAIR_FAR));
+                ops.push_back(simple(OP_PAIR_NEAR, k == nh ? 3 : 2));
+                lists_ok = true;
+            }
             add(1, 2);
         }
         add(0, 1);
@@ -746,7 +793,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
     if (!c) return HYBRID_OK;
     if (c->st) cudaStreamSynchronize(c->st);
     else cudaDeviceSynchronize();
-    Buf *all[] = {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->phi, &c->plo, &c->pd, &c->keys[0], &c->keys[1],
+    Buf *all[] = {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->phi, &c->plo, &c->pd, &c->disp, &c->keys[0], &c->keys[1],
                   &c->vals[0], &c->vals[1], &c->hist, &c->blocksum, &c->off_dev, &c->sp_dev, &c->chunks_dev,
                   &c->boxmin, &c->boxmax, &c->box, &c->sysroot, &c->status, &c->lvl, &c->nfirst, &c->ncount,
                   &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->leafof, &c->pc, &c->pD, &c->pn, &c->rec,
@@ -790,6 +837,7 @@ hybrid_status hybrid_build_tree(hybrid_ctx *c, hybrid_system *sys)
     hybrid_status r = setup_batch(c, sys, 1, false);
     if (r != HYBRID_OK) return r;
     launch_copy_in(c, (const SysIO *)c->io_dev.p, false);
+    c->lists_fresh = false;
     r = run_ops(c, {simple(OP_BUILD)});
     if (r != HYBRID_OK) return r;
     launch_copy_out(c, (const SysIO *)c->io_dev.p, true, false, false);
@@ -816,6 +864,7 @@ hybrid_status force_call(hybrid_ctx *c, hybrid_system *sys, bool soft)
     for (int d = 0; d < 3; ++d) (soft ? o.as : o.ah)[d] = a[d];
     cudaError_t e = cudaMemcpyAsync(c->io_dev.p, &o, sizeof(SysIO), cudaMemcpyHostToDevice, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    c->lists_fresh = false;
     std::vector<Op> ops = {simple(OP_WALK, soft ? 1 : 2)};
     if (soft) ops.push_back(simple(OP_PAIR_FAR));
     ops.push_back(simple(OP_PAIR_NEAR, soft ? 1 : 2));
@@ -855,9 +904,21 @@ hybrid_status hybrid_step_batched(hybrid_ctx *c, hybrid_system *sys, int n_sys, 
     if (r != HYBRID_OK) return r;
     bool valid = true;
     for (int s = 0; s < n_sys; ++s) valid = valid && sys[s].forces_valid;
+    // the lists of the previous call hold when the same arrays come back unchanged (forces_valid)
+    uint64_t sig = 1469598103934665603ull;
+    auto mixs = [&](uint64_t v) { sig = (sig ^ v) * 1099511628211ull; };
+    mixs((uint64_t)n_sys);
+    for (int s = 0; s < n_sys; ++s) {
+        mixs((uint64_t)sys[s].n);
+        mixs((uint64_t)(uintptr_t)sys[s].x);
+    }
+    const bool lists_ok = valid && c->lists_fresh && c->lists_sig == sig;
+    c->lists_fresh = false;
     launch_copy_in(c, (const SysIO *)c->io_dev.p, valid);
-    r = run_ops(c, step_ops(c, n_soft_steps, valid));
+    r = run_ops(c, step_ops(c, n_soft_steps, valid, lists_ok));
     if (r != HYBRID_OK) return r;
+    c->lists_fresh = c->p.skin > 0.0;
+    c->lists_sig = sig;
     launch_copy_out(c, (const SysIO *)c->io_dev.p, true, true, true);
     Status s;
     if ((r = read_status(c, &s)) != HYBRID_OK) return r;
@@ -880,6 +941,7 @@ hybrid_status hybrid_autotune(hybrid_ctx *c, hybrid_system *sys, int n_sys, cons
         {32, 8, 2},  {32, 8, 4},  {64, 16, 2}, {64, 16, 4}, {128, 32, 2}, {128, 32, 4}, {256, 64, 0},
         {256, 64, 2}, {128, 16, 0}, {256, 32, 0}};
     if (!c || !sys || n_sys < 1 || n_cand < 0 || (n_cand > 0 && !cand)) return HYBRID_EINVAL;
+    c->lists_fresh = false;
     const int32_t *cv = n_cand > 0 ? cand : &defaults[0][0];
     const int nc = n_cand > 0 ? n_cand : (int)(sizeof(defaults) / sizeof(defaults[0]));
     const hybrid_params saved = c->p;

@@ -14,7 +14,16 @@ struct StatePtrs {
     double *x[7];
     int32_t *id, *orig, *psys;
     void *as[3], *ah[3];
+    float4 *phi, *plo;      // FP32 hi/lo positions (precision 1)
+    float *disp;            // distance bound since the last build (skin > 0), or null
+    const SysBox *box;
 };
+
+__device__ __forceinline__ void fail(Status *st, int code, int where)
+{
+    atomicCAS(&st->code, 0, code);
+    st->where = where;
+}
 
 // system of batch position i: binary search over the offsets (S + 1 entries)
 __device__ __forceinline__ int sys_of(const int64_t *__restrict__ off, int S, int64_t i)
@@ -86,6 +95,8 @@ struct KickSpec {
     double val[4];
     int dmode;        // -1: no drift; 0: dt = dval; 2: dt = dt_soft / n_hard
     double dval;
+    int resplit;      // after the drift: new FP32 hi/lo positions and the distance bound (reused lists)
+    int where;        // op index, recorded when a particle has moved more than skin / 2
 };
 
 // Exact FP32 -> FP64 conversion of a normal number with integer operations
@@ -105,7 +116,7 @@ __device__ __forceinline__ double widen(double f) { return f; }
 // particle's update is the three products and sums per vector and nothing else.
 template <typename A>
 __global__ void __launch_bounds__(256) k_kick_drift(int64_t N, StatePtrs w, const SysParams *__restrict__ sp,
-                                                    KickSpec ks, const Status *st)
+                                                    KickSpec ks, Status *st)
 {
     if (st->code) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -126,9 +137,29 @@ __global__ void __launch_bounds__(256) k_kick_drift(int64_t N, StatePtrs w, cons
         w.x[5][i] = v2;
         if (ks.dmode >= 0) {
             const double dt = ks.dmode == 0 ? ks.dval : P.dt_hard;
-            w.x[0][i] = __dadd_rn(w.x[0][i], __dmul_rn(dt, v0));
-            w.x[1][i] = __dadd_rn(w.x[1][i], __dmul_rn(dt, v1));
-            w.x[2][i] = __dadd_rn(w.x[2][i], __dmul_rn(dt, v2));
+            const double x0 = __dadd_rn(w.x[0][i], __dmul_rn(dt, v0));
+            const double x1 = __dadd_rn(w.x[1][i], __dmul_rn(dt, v1));
+            const double x2 = __dadd_rn(w.x[2][i], __dmul_rn(dt, v2));
+            w.x[0][i] = x0;
+            w.x[1][i] = x1;
+            w.x[2][i] = x2;
+            if (ks.resplit) {
+                // the pair kernels' copy of the moved positions, and the distance of this drift (from the old
+                // and new hi/lo copies: hi differences are exact) added to the bound since the last build
+                const SysBox &b = w.box[w.psys[i]];
+                float h0, h1, h2, l0, l1, l2;
+                grid_split(x0, b.lo[0], b, h0, l0);
+                grid_split(x1, b.lo[1], b, h1, l1);
+                grid_split(x2, b.lo[2], b, h2, l2);
+                const float4 oh = w.phi[i], ol = w.plo[i];
+                const float d0 = (h0 - oh.x) + (l0 - ol.x), d1 = (h1 - oh.y) + (l1 - ol.y), d2 = (h2 - oh.z) + (l2 - ol.z);
+                w.phi[i] = make_float4(h0, h1, h2, oh.w);
+                w.plo[i] = make_float4(l0, l1, l2, 0.0f);
+                // rounded up by a few units in the last place: a bound, not an estimate
+                const float moved = w.disp[i] + sqrtf(d0 * d0 + d1 * d1 + d2 * d2) * 1.000001f + 1e-30f;
+                w.disp[i] = moved;
+                if (moved > P.half_skinf) fail(st, ST_SKIN, ks.where);
+            }
         }
     }
 }
@@ -230,6 +261,10 @@ StatePtrs state_ptrs(hybrid_ctx *c)
         w.as[d] = c->acc_s[d].p;
         w.ah[d] = c->acc_h[d].p;
     }
+    w.phi = (float4 *)c->phi.p;
+    w.plo = (float4 *)c->plo.p;
+    w.disp = (float *)c->disp.p;
+    w.box = (const SysBox *)c->box.p;
     return w;
 }
 
@@ -255,9 +290,11 @@ void launch_copy_out(hybrid_ctx *c, const SysIO *d_io, bool state, bool acc_s, b
 }
 
 void launch_kick_seq(hybrid_ctx *c, int n, const int *which, const int *mode, const double *val, int dmode,
-                     double dval)
+                     double dval, bool resplit)
 {
     KickSpec ks;
+    ks.resplit = resplit && dmode >= 0 && c->p.precision == 1 && c->p.skin > 0.0;
+    ks.where = c->op;
     ks.n = n;
     for (int k = 0; k < 4; ++k) {
         ks.which[k] = k < n ? which[k] : 0;

@@ -9,9 +9,10 @@
 // FP32 form. Work item = (group, run of at most item_len consecutive entries
 // of one of the group's lists), written by the walk and pulled from a global
 // counter. One warp per work item: sources are staged, 64 at a time, into the
-// warp's shared-memory tile as float4 {x, y, z, m} relative to the group's
-// reference point (the hi part of its first sink: on the hi grid, so hi - c
-// is exact); the gathers run ahead of their use (see the staging ring). A group of n sinks uses
+// warp's shared-memory tile relative to the group's reference point (the hi
+// part of its first sink: on the hi grid, so hi - c is exact), as {x, y, z, m}
+// or, for far sources, in the expanded form of body_exp2; the gathers run
+// ahead of their use (see the staging ring). A group of n sinks uses
 // lpc = ceil(n / KS) lanes per copy with KS sinks per lane in registers, and
 // copies = 32 / lpc copies of the group split the sources (source j goes to
 // copy j mod copies) and are added at the end. A group with one chunk stores
@@ -426,11 +427,15 @@ __device__ __forceinline__ void far_tile(const Stage &S, int nt, int copy, int c
 // sum_j m_j r_j^-3 (s_j - k) = sum_j r_j^-3 (m_j s_j) - k sum_j r_j^-3 m_j, so
 // a source stages {-2s, |s|^2, m s, m} and a pair costs the sum c + Q, three
 // fma for r^2, rsqrt, two mul for r^-3 and four fma: 10 FP32 lane operations
-// against 12 for body_far. The walk takes a cell only beyond its opening
-// radius and beyond R2 + b_max, and a far particle only beyond R2 of the
-// sinks' box, so r is not small against |s| and |k| and the cancellation in
-// r^2 stays a few units of FP32 rounding. Without a hard part a sink meets its
-// neighbours among the far particles: those items keep body_far.
+// against 12 for body_far. The rounding of r^2 is at most about
+// 4 u (|s| + |k|)^2 <= 4 u (r + 2 |k|)^2 (u = 2^-24). With a hard part the walk
+// takes a cell only beyond R2 + b_max (and beyond its opening radius) and a far
+// particle only beyond R2 of the sinks' box, so r >= R2, and with every sink
+// within 64 R2 of the reference point the rounding stays below ~4e-3 of r^2
+// (r^2 cannot change sign; typical pairs sit far from that bound). Other items
+// keep body_far: without a hard part a cell of one or a few particles can be
+// taken right next to the sinks, and a very large group in sparse outskirts
+// can have far sources at R2 from its edge.
 // Q = |k|^2 + eps^2 per sink; the caller subtracts k FM from A at the end.
 __device__ __forceinline__ void body_exp2(uint64_t NX, uint64_t NY, uint64_t NZ, uint64_t C2, uint64_t MX, uint64_t MY,
                                            uint64_t MZ, uint64_t M2, uint64_t SX, uint64_t SY, uint64_t SZ, uint64_t Q,
@@ -543,9 +548,15 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
                     AX[p] = AY[p] = AZ[p] = 0ull;
                 }
                 const uint64_t E2 = pk2(H.eps2, H.eps2);
-                // the expanded form: cells always; far particles when there is a hard part (then every
-                // far particle is at least R2 from the sinks' box; without one, a sink meets its neighbours)
-                if (H.eps2 > 0.0f && (d.e1 <= d.Lc || P.has_hard)) {
+                // the expanded form only with a hard part (then every far source is at least R2 from the sinks'
+                // box; without one, cells and particles can sit next to the sinks) and for sinks within 64 R2
+                // of the reference point: the rounding of r^2 stays below 4 u (1 + 2 * 64)^2 ~ 4e-3 of r^2
+                float k2 = 0.0f;
+#pragma unroll
+                for (int kk = 0; kk < KS; ++kk) k2 = fmaxf(k2, fmaf(sx[kk], sx[kk], fmaf(sy[kk], sy[kk], sz[kk] * sz[kk])));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) k2 = fmaxf(k2, __shfl_xor_sync(0xffffffffu, k2, o));
+                if (H.eps2 > 0.0f && P.has_hard && k2 <= 4096.0f * H.R2sq) {
                     uint64_t Q[KP], FM[KP];
 #pragma unroll
                     for (int p = 0; p < KP; ++p) {

@@ -131,17 +131,6 @@ __device__ __forceinline__ uint32_t cell_coord(double p, double lo, double scale
     return (uint32_t)t;
 }
 
-// FP32 hi/lo copy of a coordinate relative to the root corner: hi = the
-// nearest multiple of u (at most 2^20 steps: exact in FP32), lo = the rest
-// (exact in FP64, then rounded to FP32, |lo| <= u/2).
-__device__ __forceinline__ void grid_split(double x, double lo0, const SysBox &b, float &h, float &l)
-{
-    const double xp = __dsub_rn(x, lo0);
-    const double hh = __dmul_rn(rint(__dmul_rn(xp, b.inv_u)), b.u);
-    h = (float)hh;
-    l = (float)__dsub_rn(xp, hh);
-}
-
 // Also finishes the root cubes (from the atomic min/max) and stores them.
 __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restrict__ x, const double *__restrict__ y,
                                               const double *__restrict__ z, const int32_t *__restrict__ psys, int S,
@@ -382,6 +371,7 @@ struct PermArgs {
     const uint32_t *src;
     float4 *phi, *plo;
     double4_32a *pd;
+    float *disp;          // zeroed: distance moved since this build (reused lists), or null
     const int32_t *psys;
     const SysBox *box;
     int64_t N;
@@ -409,6 +399,7 @@ __global__ void __launch_bounds__(256) k_permute(PermArgs a, const Status *st)
             a.plo[i] = make_float4(l[0], l[1], l[2], 0.0f);
         }
         if (a.pd) a.pd[i] = make_double4_32a(v[0], v[1], v[2], v[6]);
+        if (a.disp) a.disp[i] = 0.0f;
     }
 }
 
@@ -1155,7 +1146,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a, const Status *st)
             const double bm = __longlong_as_double((long long)a.bmax[c]);
             if (P.mac == 1) rb = 0.5 * bm + sqrt(0.25 * bm * bm + sqrt(3.0 * a.B2[c] / P.a_err));
             else rb = (P.theta > 0.0) ? sd / P.theta + delta : INFINITY;
-            hr = P.R2 + bm;   // Eq. (15) radius
+            hr = P.R2 + P.skin + bm;   // Eq. (15) radius (plus the skin of reused lists)
             const double sacc = fmax(rb, hr);
             a.crit[c] = make_float2((float)(sacc * sacc), P.has_hard ? (float)(hr * hr) : -1.0f);
             a.nD[c] = make_double4_32a(a.cx[c], a.cy[c], a.cz[c], a.M[c]);
@@ -1172,7 +1163,7 @@ __global__ void __launch_bounds__(256) k_finalize(FinArgs a, const Status *st)
             float rbf;
             if (P.mac == 1) rbf = 0.5f * bm + sqrtf(0.25f * bm * bm + sqrtf(3.0f * B.w / (float)P.a_err));
             else rbf = (P.theta > 0.0) ? sdf / (float)P.theta + df : INFINITY;
-            const float hrf = P.R2f + bm;
+            const float hrf = P.R2f + P.skinf + bm;
             const float sacc = fmaxf(rbf, hrf);
             a.crit[c] = make_float2(sacc * sacc, P.has_hard ? hrf * hrf : -1.0f);
             // FP64 copies (all lanes busy): moments, b_max, geometry
@@ -1380,6 +1371,7 @@ void launch_permute(hybrid_ctx *c)
     a.phi = c->p.precision == 1 ? (float4 *)c->phi.p : nullptr;
     a.plo = c->p.precision == 1 ? (float4 *)c->plo.p : nullptr;
     a.pd = c->p.precision == 0 ? (double4_32a *)c->pd.p : nullptr;
+    a.disp = c->p.skin > 0.0 ? (float *)c->disp.p : nullptr;
     a.psys = (const int32_t *)c->psys.p;
     a.box = (const SysBox *)c->box.p;
     a.N = N;

@@ -40,6 +40,7 @@ class hybrid_params(C.Structure):
         ("dt_soft", C.c_double), ("a_err", C.c_double),
         ("n_hard", C.c_int32), ("n_leaf", C.c_int32), ("n_crit", C.c_int32),
         ("precision", C.c_int32), ("mac", C.c_int32), ("threads_per_group", C.c_int32), ("tile_depth", C.c_int32),
+        ("skin", C.c_double),
     ]
 
 
@@ -138,11 +139,12 @@ class Params:
     mac: int = 0
     threads_per_group: int = 0
     tile_depth: int = 0
+    skin: float = 0.0
 
     def c(self) -> hybrid_params:
         return hybrid_params(self.G, self.eps, self.theta, self.R1, self.R2, self.dt_soft, self.a_err, self.n_hard,
                              self.n_leaf, self.n_crit, self.precision, self.mac, self.threads_per_group,
-                             self.tile_depth)
+                             self.tile_depth, self.skin)
 
 
 def _ptr(t):

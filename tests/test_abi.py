@@ -47,7 +47,8 @@ def test_invalid_params_rejected_without_gpu(lib):
     bad = [
         dict(eps=-1.0), dict(R1=0.2, R2=0.1), dict(R1=0.1, R2=0.1), dict(n_hard=0), dict(n_leaf=0),
         dict(n_crit=0), dict(precision=2), dict(mac=1, a_err=0.0), dict(theta=-0.1),
-        dict(threads_per_group=-1), dict(tile_depth=1), dict(tile_depth=5),
+        dict(threads_per_group=-1), dict(tile_depth=1), dict(tile_depth=5), dict(skin=-0.1),
+        dict(skin=float("inf")), dict(skin=0.01, precision=0, R1=0.1, R2=0.2), dict(skin=0.01, R1=0.0, R2=0.0),
     ]
     for kw in bad:
         p = hybrid.Params(**kw).c()
@@ -61,7 +62,9 @@ def test_invalid_params_rejected_without_gpu(lib):
 
 
 def test_struct_layout_matches_header():
-    # hybrid_params: 7 doubles + 7 int32 = 84 -> padded to 88; hybrid_system: int64 + 14 pointers + pointer + int32
+    # hybrid_params: 7 doubles + 7 int32 (84, padded to 88) + 1 double = 96; hybrid_system: int64 + 14 pointers +
+    # pointer + int32
     from paper_1406_6158_gb300 import hybrid
-    assert C.sizeof(hybrid.hybrid_params) == 88
+    assert C.sizeof(hybrid.hybrid_params) == 96
+    assert hybrid.hybrid_params.skin.offset == 88
     assert C.sizeof(hybrid.hybrid_system) == 8 + 8 * 15 + 8

@@ -343,6 +343,61 @@ def test_step_fp32_close_to_oracle(H, kw):
         assert np.max(np.abs(out[k][o] - ost[k][q])) <= 1e-8
 
 
+@pytest.mark.parametrize("skin", [0.05, 1e-7], ids=["reused", "skin_exceeded_rebuilds"])
+def test_reused_lists_follow_the_oracle(H, skin):
+    # skin > 0: hard steps 1..n-1 reuse the tree and the neighbour lists of the last build (an option outside
+    # the paper). At theta = 0 the soft force is direct summation whichever lists carry it and the hard force
+    # takes every pair within R2, so three soft steps must follow the oracle (which rebuilds at every hard
+    # step) to FP32 force rounding. With a skin of 1e-7 the first drift moves particles beyond skin / 2 and the
+    # step falls back to rebuilding; with 0.05 the reuse holds and the step launches fewer kernels.
+    n = 2048
+    st = ics.plummer(n, 8)
+    st["id"] = np.arange(n, dtype=np.int64)
+    launches = []
+    for sk in (0.0, skin):
+        P = plummer_params(n, 1, theta=0.0, dt_soft=1 / 128, n_hard=4, skin=sk)
+        ctx = H.Context(P)
+        s = H.System(st, precision=1)
+        ctx.hybrid_step(s, 0)
+        l0 = ctx.hybrid_launch_count()
+        for _ in range(3):
+            ctx.hybrid_step(s, 1)
+        launches.append(ctx.hybrid_launch_count() - l0)
+        out = s.numpy()
+        ost = {k: np.array(v, copy=True) for k, v in st.items()}
+        oracle.hybrid_steps(ost, oparams(P), 3)
+        o, q = np.argsort(out["id"]), np.argsort(ost["id"])
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            assert np.max(np.abs(out[k][o] - ost[k][q])) <= 1e-8, (sk, k)
+        ctx.close()
+    if skin > 1e-3:
+        assert launches[1] < launches[0]
+    else:
+        assert launches[1] >= launches[0]
+
+
+def test_reused_lists_close_to_rebuilds_at_theta(H):
+    # theta = 0.5: the skin changes the tree opening (cells are taken only beyond R2 + skin + b_max), so the
+    # soft force differs from the rebuilt one by less than the tree error (~1e-3 rms); over three soft steps of
+    # 1/128 that moves positions by far less than 1e-6. The graph path (a stream of its own) replays the reuse.
+    n = 6000
+    st = ics.plummer(n, 31)
+    res = []
+    for sk in (0.0, 0.04):
+        P = plummer_params(n, 1, dt_soft=1 / 128, n_hard=4, skin=sk)
+        ctx = H.Context(P, torch.cuda.Stream())
+        s = H.System(st, precision=1)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            ctx.hybrid_step(s, 1)
+        torch.cuda.synchronize()
+        out = s.numpy()
+        res.append({k: out[k][np.argsort(out["id"])] for k in ("x", "y", "z", "vx")})
+        ctx.close()
+    for k in ("x", "y", "z"):
+        assert np.max(np.abs(res[0][k] - res[1][k])) <= 1e-6, k
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_batched_equals_alone(H, prec):
     sizes = [1000, 5003, 2500]
