@@ -30,10 +30,10 @@ sys.path.insert(0, ROOT)
 N_DEFAULT = 1 << 17
 METRIC = "particle-steps/s"
 FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul, 3 fma (by convention 20)
-# DRAM bytes (read + write) of one far-pair launch on this workload, from an ncu capture of the kernel
-# variant the key names (n_crit, threads per group, staging depth); see profiles/far_pair_plummer131k.md.
-# Reported as the roofline's traffic only when the autotuner picks that same variant.
-FAR_TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) of one far-pair launch on this workload, from ncu captures of the kernel
+# variants the keys name (n_crit, threads per group, staging depth); see profiles/far_pair_plummer131k.md.
+# Reported as the roofline's traffic only when the autotuner picks one of these variants.
+FAR_TRAFFIC_BYTES = {(128, 16, 0): 57.009e6, (128, 32, 2): 56.80e6, (128, 32, 4): 56.78e6}
 L2_FLUSH_BYTES = 256 << 20
 ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
 # Verlet skin of the reused-list measurement: twice the distance the fastest particle of the Plummer sphere
@@ -415,6 +415,23 @@ def run_c5(args):
     return 0
 
 
+def hbm_stages(n, n_hard, ms):
+    """Achieved HBM bandwidth of the memory-bound stages from their live times per soft step and their
+    algorithmic bytes per particle: key sort per build 36 (keys: x, y, z in, key and index out) + 8 (digit
+    counts) + 8 passes x 24 (key and index in and out); kick + drift 108 per drift launch (v 24, a 12, x 24 in;
+    v 24, x 24 out). n_hard builds and drift launches per soft step."""
+    peak = float(measured_peaks().get("hbm_gbs", 6655.6))
+    out = {}
+    for name, per_particle in (("sort", 36 + 8 + 8 * 24), ("kick_drift", 108)):
+        t = ms.get(name)
+        if not t:
+            continue
+        gbs = n * per_particle * n_hard / (t / 1e3) / 1e9
+        out[name] = {"bytes_per_particle_per_launch": per_particle, "launches_per_step": n_hard, "GB/s": gbs,
+                     "frac_of_measured_hbm": gbs / peak}
+    return out
+
+
 def run_c3(args):
     """Large single system: Hernquist sphere N=2^24 (seed 2, a=1, r<=100), eps=1/512, theta=0.4, R1=3eps,
     R2=6eps, dt_s=1/128, n_hard=8, FP32 pairs on FP64 state."""
@@ -486,6 +503,7 @@ def run_c3(args):
         "kernel_ms_per_step": {nm: kinds[k][0] / args.steps for k, nm in enumerate(names)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "kernel": "k_pair_f32 far (cells + far particles, soft force)"},
+        "hbm_stages": hbm_stages(n, P.n_hard, {nm: kinds[k][0] / args.steps for k, nm in enumerate(names)}),
         "gpu_launches": launches, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

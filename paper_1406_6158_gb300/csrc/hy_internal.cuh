@@ -91,7 +91,7 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
 constexpr uint32_t ITEM_MULTI = 0x80000000u;
-constexpr int LCH_FAR = 512, LCH_NEAR = 256;
+constexpr int LCH_FAR = 512, LCH_NEAR = 256, LCH_NEAR_SMALL = 128;
 
 // Entries per work item of a group of n sinks: lch for n >= 64, longer runs
 // (up to 8 lch) for smaller groups, so that items cost about the same
@@ -146,7 +146,7 @@ struct hybrid_ctx {
     std::vector<hy::Chunk> h_chunks;
     std::vector<hy::SysIO> h_io;
     int nchunks = 0;
-    int ipt = 16, tile = 4096;   // radix tile: 8 warps x 32 lanes x ipt keys, sized to fill the GPU
+    int ipt = hy::RS_IPT_MAX, tile = hy::RS_TILE_MAX;   // radix tile: 8 warps x 32 lanes x ipt keys, sized to fill the GPU
     bool tree_valid = false, have_soft = false, have_hard = false;
     // reused neighbour lists (skin > 0): the lists of the last walk still hold for the working state of the
     // batch with this signature (set at the end of a step, cleared by anything else that builds or walks)
