@@ -760,18 +760,23 @@ def main():
         kr = max(3, args.steps // 3)
         evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(kr)]
         l0 = ctx2.hybrid_launch_count()
+        clocks2 = ClockSampler(local)
         barrier()
+        clocks2.start()
         for k in range(kr):
             flush.zero_()
             evr[k][0].record(stream)
             ctx2.hybrid_step(s2, 1)
             evr[k][1].record(stream)
         barrier()
-        tr = sum(a.elapsed_time(b) for a, b in evr) / 1e3
+        clk2 = clocks2.stop()
+        per = [a.elapsed_time(b) for a, b in evr]
+        tr = sum(per) / 1e3
         r_e1 = sum(ctx2.hybrid_energy(s2))
         rv, tr = job_rate(w["n"] * kr, tr, dist)
         reuse = {"skin": REUSE_SKIN, "value": rv, "unit": METRIC, "ms_per_step": 1e3 * tr / kr, "steps": kr,
                  "gpu_launches_per_step": (ctx2.hybrid_launch_count() - l0) / kr,
+                 "ms_median": sorted(per)[len(per) // 2], "ms_max": max(per), "clocks": clk2,
                  "energy_rel_drift": abs(r_e1 - r_e0) / abs(r_e0), "energy_soft_steps": 1 + args.warmup + kr,
                  "note": "hard steps 1..n-1 reuse the tree and neighbour lists of the last build (lists to R2 + "
                          "skin); not the paper's scheme, which rebuilds every hard step"}
