@@ -291,6 +291,9 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
         }
         __syncthreads();
         const int d = threadIdx.x;
+        // loads that do not depend on the look-back go out before it
+        const uint32_t cd = counts[(size_t)ch.sys * 2048 + pass * 256 + d];
+        const int64_t s0 = chunks[ch.first_chunk].start;
         uint32_t run = 0;   // tile count of digit d; whist becomes the exclusive prefix over the warps
         for (int ww = 0; ww < RS_WARPS; ++ww) {
             const uint32_t cnt = whist[ww][d];
@@ -312,7 +315,6 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
         }
         // exclusive prefixes over digits, in one block scan: the system's counts (high 32 bits) and the
         // tile's counts (low 32 bits; at most 2048, so no carry crosses over)
-        const uint32_t cd = counts[(size_t)ch.sys * 2048 + pass * 256 + d];
         const uint64_t both = ((uint64_t)cd << 32) | run;
         uint64_t incl = both;
 #pragma unroll
@@ -341,7 +343,6 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
             }
         }
         __syncthreads();
-        const int64_t s0 = chunks[ch.first_chunk].start;
 #pragma unroll
         for (int it = 0; it < IPT; ++it) {
             const int lp = it * 256 + threadIdx.x;
