@@ -343,25 +343,29 @@ def test_step_fp32_close_to_oracle(H, kw):
         assert np.max(np.abs(out[k][o] - ost[k][q])) <= 1e-8
 
 
+@pytest.mark.parametrize("graphs", [False, True], ids=["eager", "graphs"])
 @pytest.mark.parametrize("skin", [0.05, 1e-7], ids=["reused", "skin_exceeded_rebuilds"])
-def test_reused_lists_follow_the_oracle(H, skin):
+def test_reused_lists_follow_the_oracle(H, skin, graphs):
     # skin > 0: hard steps 1..n-1 reuse the tree and the neighbour lists of the last build (an option outside
     # the paper). At theta = 0 the soft force is direct summation whichever lists carry it and the hard force
     # takes every pair within R2, so three soft steps must follow the oracle (which rebuilds at every hard
     # step) to FP32 force rounding. With a skin of 1e-7 the first drift moves particles beyond skin / 2 and the
-    # step falls back to rebuilding; with 0.05 the reuse holds and the step launches fewer kernels.
+    # step falls back to rebuilding; with 0.05 the reuse holds and the step launches fewer kernels. On a stream
+    # of its own the step replays a captured graph, and a fallback resumes eagerly after the graph.
     n = 2048
     st = ics.plummer(n, 8)
     st["id"] = np.arange(n, dtype=np.int64)
     launches = []
     for sk in (0.0, skin):
         P = plummer_params(n, 1, theta=0.0, dt_soft=1 / 128, n_hard=4, skin=sk)
-        ctx = H.Context(P)
+        ctx = H.Context(P, torch.cuda.Stream() if graphs else None)
         s = H.System(st, precision=1)
+        torch.cuda.synchronize()
         ctx.hybrid_step(s, 0)
         l0 = ctx.hybrid_launch_count()
         for _ in range(3):
             ctx.hybrid_step(s, 1)
+        torch.cuda.synchronize()
         launches.append(ctx.hybrid_launch_count() - l0)
         out = s.numpy()
         ost = {k: np.array(v, copy=True) for k, v in st.items()}
