@@ -172,7 +172,9 @@ hybrid_status hybrid_step_batched(hybrid_ctx *ctx, hybrid_system *sys, int n_sys
  * soft + (n_hard - 1) x hard. The fastest candidate becomes the context's
  * setting for later calls. ms_out (optional, host, n_cand doubles) receives
  * the estimates, best_out (optional) the index of the choice. The systems'
- * arrays are read, not written. EINVAL for an invalid candidate. */
+ * arrays are read, not written. EINVAL for an invalid candidate. With a
+ * skin (see hybrid_params) the estimate still counts a build and a walk per
+ * hard step, which reused lists skip. */
 hybrid_status hybrid_autotune(hybrid_ctx *ctx, hybrid_system *sys, int n_sys, const int32_t *cand, int n_cand,
                               double *ms_out, int32_t *best_out);
 
