@@ -178,21 +178,26 @@ def run_reference(args, w):
     p = oracle.Params(eps=w["eps"], theta=w["theta"], R1=w["R1"], R2=w["R2"], dt_soft=w["dt_soft"],
                       n_hard=w["n_hard"], n_leaf=w["n_leaf"], n_crit=w["n_crit"])
     a_s, a_h = oracle.forces(st, p)
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 3)):
         a_s, a_h = oracle.hybrid_steps(st, p, 1, a_s, a_h)
+    # whole soft steps of the workload, at most args.steps of them and as many as fit in the time box, so that
+    # the run ends within a few minutes (one soft step of the oracle takes most of a second here)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    done = 0
+    while done < args.steps and (done == 0 or time.perf_counter() - t0 < args.ref_max_seconds):
         a_s, a_h = oracle.hybrid_steps(st, p, 1, a_s, a_h)
+        done += 1
     t = time.perf_counter() - t0
-    v = w["n"] * args.steps / t
+    v = w["n"] * done / t
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "steps_timed": done, "warmup": args.warmup, "ms_per_step": 1e3 * t / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(w), "N": w["n"], "l2": "n/a (CPU)"},
         "cpu_baseline": {"value": v, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
-                         "sample": "%d whole soft steps of the workload after %d warm-up steps" %
-                                   (args.steps, args.warmup)},
+                         "sample": "%d whole soft steps of the workload (of %d asked, time box %.0f s) after %d "
+                                   "warm-up steps" % (done, args.steps, args.ref_max_seconds,
+                                                      min(args.warmup, 3))},
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -640,6 +645,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-reuse", action="store_true", help="skip the reused-neighbour-list measurement")
+    ap.add_argument("--ref-max-seconds", type=float, default=120.0,
+                    help="time box of the reference arm's timed steps (the oracle on the host cores)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per soft-pair launch from an ncu capture of this workload")
     ap.add_argument("--workload", default="single", choices=["single", "batched", "served", "large", "paper"],
