@@ -12,6 +12,10 @@ kernels on FP64 state. Prints one JSON line.
 --gpus N > 1 runs N independent replicas (torchrun, one rank per GPU); the
 path has no exchange step, so there is no collective on the data path.
 --impl reference times the CPU FP64 oracle on the host cores instead.
+Beside the headline the line carries the same workload with reused trees and
+neighbour lists (a Verlet skin; not the paper's scheme). Other workloads:
+--workload large | batched | served | paper (hybrid against normal tree with
+the paper's parameter set).
 """
 from __future__ import annotations
 
