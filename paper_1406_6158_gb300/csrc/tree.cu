@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restric
 // words backwards until it meets an inclusive prefix (a chained scan with
 // look-back), and publishes its own inclusive prefix. A key's destination is
 // the system's start + the system's count of smaller digits + the earlier
-// tiles' count of its digit + its rank in the tile. Tiles only wait on tiles
+// tiles' count of its digit + its rank in the tile; the tile is reordered in
+// shared memory by (digit, rank) first, so that consecutive threads write
+// consecutive addresses of one digit's run. Tiles only wait on tiles
 // with smaller tickets, which were claimed by running blocks and publish
 // their counts before they wait on anything; every wait is bounded.
 // ---------------------------------------------------------------------------
