@@ -68,3 +68,23 @@ def test_struct_layout_matches_header():
     assert C.sizeof(hybrid.hybrid_params) == 96
     assert hybrid.hybrid_params.skin.offset == 88
     assert C.sizeof(hybrid.hybrid_system) == 8 + 8 * 15 + 8
+
+
+def test_status_codes_match_header():
+    # the binding's status constants are the header's enum values, in order
+    from paper_1406_6158_gb300 import hybrid
+    text = open(os.path.join(ROOT, "include", "hybrid.h")).read()
+    enum = dict((k, int(v)) for k, v in re.findall(r"HYBRID_([A-Z]+)\s*=\s*(\d+)", text))
+    for name in ("OK", "EINVAL", "ENOMEM", "ECUDA", "ECAPACITY", "ETIMEOUT", "ETOOLARGE"):
+        assert getattr(hybrid, name) == enum[name], name
+
+
+def test_params_fields_match_header():
+    # hybrid_params fields in the header's order (the ctypes struct mirrors it)
+    from paper_1406_6158_gb300 import hybrid
+    text = open(os.path.join(ROOT, "include", "hybrid.h")).read()
+    body = text[text.index("typedef struct {\n    double G"):text.index("} hybrid_params;")]
+    names = re.findall(r"(?:double|int32_t)\s+([^;]+);", body)
+    fields = [f.strip() for group in names for f in group.split(",")]
+    assert fields == [f for f, _ in hybrid.hybrid_params._fields_]
+
