@@ -88,3 +88,15 @@ def test_params_fields_match_header():
     fields = [f.strip() for group in names for f in group.split(",")]
     assert fields == [f for f, _ in hybrid.hybrid_params._fields_]
 
+
+def test_system_fields_match_header():
+    from paper_1406_6158_gb300 import hybrid
+    text = open(os.path.join(ROOT, "include", "hybrid.h")).read()
+    end = text.index("} hybrid_system;")
+    body = text[text.rindex("typedef struct {", 0, end):end]
+    fields = []
+    for decl in re.findall(r"^\s+([^;]+);", body, flags=re.M):
+        names = decl.split(None, 1)[1] if not decl.startswith("const") else decl.split(None, 2)[2]
+        fields += [f.strip().lstrip("*") for f in names.split(",")]
+    assert fields == [f for f, _ in hybrid.hybrid_system._fields_]
+
