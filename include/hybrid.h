@@ -60,7 +60,8 @@ typedef enum {
  * mac      0: opening angle theta; 1: absolute MAC with a_err (Eq. 5-6)
  * threads_per_group: lanes that share one copy of a sink group in the FP32
  *          pair kernels; each lane then keeps ceil(n_crit / threads_per_group)
- *          sinks (1, 2 or 4) in registers. 0 = built-in default.
+ *          sinks in registers (1, 2, 4 or 8; 4 at most in the near kernel).
+ *          0 = built-in default.
  * tile_depth: shared-memory staging depth of the FP32 far pair kernel: source
  *          gathers run tile_depth - 1 tiles of 64 list entries ahead of their
  *          use; 2, 3 or 4, 0 = built-in default (3).
@@ -79,10 +80,12 @@ typedef enum {
  *          slightly more accurate tree opening). The n - 1 hard steps that
  *          follow reuse that tree, its groups and its neighbour lists: their
  *          hard force is the same sum over the current positions of the
- *          listed neighbours. Each drift adds |v| dt to a per-particle bound
- *          of the distance moved since the last build; when one exceeds
- *          skin / 2 a pair within R2 could be missing, and that hard step
- *          rebuilds the tree and the lists first (inside the same call). */
+ *          listed neighbours. Each drift adds the distance it moved a
+ *          particle (rounded up) to a per-particle bound since the last
+ *          build; when one exceeds skin / 2 a pair within R2 could be
+ *          missing, and that hard step and the later ones of the same call
+ *          rebuild the tree and the lists first. EINVAL when skin < 0, or
+ *          skin > 0 without precision 1 and a hard part. */
 typedef struct {
     double G, eps, theta, R1, R2, dt_soft, a_err;
     int32_t n_hard, n_leaf, n_crit;
