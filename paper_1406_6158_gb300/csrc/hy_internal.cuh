@@ -91,7 +91,7 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
 constexpr uint32_t ITEM_MULTI = 0x80000000u;
-constexpr int LCH_FAR = 512, LCH_NEAR = 256, LCH_NEAR_SMALL = 64;
+constexpr int LCH_FAR = 512, LCH_NEAR = 512, LCH_NEAR_SMALL = 64;
 
 // Entries per work item of a group of n sinks: lch for n >= 64, longer runs
 // (up to 8 lch) for smaller groups, so that items cost about the same
