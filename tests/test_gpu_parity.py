@@ -552,3 +552,34 @@ def test_c2_full_size_sampled(H):
     nz = np.linalg.norm(a_h[mask], axis=1) > 0
     eh = np.linalg.norm(g_h - a_h[mask], axis=1)[nz] / np.linalg.norm(a_h[mask], axis=1)[nz]
     assert np.percentile(eh, 99) <= 1e-5
+
+
+def test_large_hernquist_sampled(H):
+    # Hernquist N = 2^21 (seed 2) with the large workload's parameters (eps 1/512, theta 0.4, R1 = 3 eps,
+    # R2 = 6 eps, n_crit 256): radix tiles of 2048 keys, near work items of the large-batch length; forces of
+    # 200 sampled groups against the oracle on the same tree
+    n = 1 << 21
+    st = ics.hernquist(n, 2)
+    eps = 1 / 512
+    P = plummer_params(n, 1, eps=eps, theta=0.4, R1=3 * eps, R2=6 * eps, n_crit=256)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_build_tree(s)
+    ctx.hybrid_soft_force(s)
+    ctx.hybrid_hard_force(s)
+    out = s.numpy()
+    T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
+    assert np.array_equal(T.perm, np.arange(n))
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(T.ng, 200, replace=False))
+    a_s, a_h, _, _ = T.forces(groups=sel)
+    mask = ~np.isnan(a_s[:, 0])
+    g_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)[mask]
+    g_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)[mask]
+    es = np.linalg.norm(g_s - a_s[mask], axis=1) / np.linalg.norm(a_s[mask], axis=1)
+    assert np.percentile(es, 99) <= 1e-5, np.percentile(es, 99)
+    nz = np.linalg.norm(a_h[mask], axis=1) > 0
+    eh = np.linalg.norm(g_h - a_h[mask], axis=1)[nz] / np.linalg.norm(a_h[mask], axis=1)[nz]
+    assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
+    ctx.close()
+
