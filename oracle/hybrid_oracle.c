@@ -676,8 +676,9 @@ void orc_tree_forces(const orc_tree *t, int64_t nsel, const int64_t *sel, int32_
     }
 }
 
-/* Interactions the same-tree force evaluates (sink-source pairs, j = i not
- * counted): soft = |group| * (cells + particles), hard = |group| * hard. */
+/* Interactions the same-tree force evaluates, as sink-source pairs of the
+ * lists: soft = |group| * (cells + particles), hard = |group| * hard, summed
+ * over groups. A sink's pair with itself is counted (it adds 0 to the force). */
 void orc_interactions(const orc_tree *t, int32_t mode, int64_t *soft, int64_t *hard)
 {
     int64_t s = 0, h = 0;

@@ -303,6 +303,85 @@ def test_theta_zero_lists_are_all_particles():
         assert len(cells) == 0 and np.array_equal(np.sort(parts), np.arange(T.n))
 
 
+def load_lists_golden():
+    params, parts, order, groups = {}, {}, [], {}
+    for line in open(os.path.join(GOLDEN, "lists_small.txt")):
+        w = line.split()
+        if not w or w[0].startswith("#"):
+            continue
+        if w[0] == "params":
+            params = {w[k]: float(w[k + 1]) for k in range(1, len(w), 2)}
+        elif w[0] == "particle":
+            parts[w[1]] = tuple(float(v) for v in w[2:5])
+        elif w[0] == "order":
+            order = w[1:]
+        elif w[0] == "group":
+            i_c, i_p, i_h = w.index("cells"), w.index("particles"), w.index("hard")
+            cells = sorted((int(c.split(":")[0]), frozenset(c.split(":")[1].split(","))) for c in w[i_c + 1:i_p])
+            groups[w[1]] = (cells, sorted(w[i_p + 1:i_h]), sorted(w[i_h + 1:]))
+    return params, parts, order, groups
+
+
+def test_walk_lists_golden():
+    # hand-derived lists (tests/golden/lists_small.txt): one cell taken exactly at r = r_b (strict opening),
+    # one opened just inside r_b, one refused by the R2 + b_max test of Eq. (15) alone
+    prm, parts, order, want = load_lists_golden()
+    labels = list(parts)
+    P = np.array([parts[k] for k in labels])
+    p = oracle.Params(theta=prm["theta"], R1=prm["R1"], R2=prm["R2"], n_leaf=int(prm["n_leaf"]),
+                      n_crit=int(prm["n_crit"]))
+    T = oracle.Tree(P[:, 0], P[:, 1], P[:, 2], np.ones(len(labels)), p)
+    assert [labels[i] for i in T.perm] == order
+    name = [labels[i] for i in T.perm]               # sorted position -> label
+    gid = {name[T.first[c]]: g for g, c in enumerate(T.gnode)}
+    sel = [gid[k] for k in want]
+    for (gname, (cells, plist, hlist)), (gc, gp, gh) in zip(want.items(), T.walk(sel)):
+        got_cells = sorted((int(T.level[c]), frozenset(name[T.first[c] + i] for i in range(T.count[c])))
+                           for c in gc)
+        assert got_cells == cells, gname
+        assert sorted(name[i] for i in gp) == plist, gname
+        assert sorted(name[i] for i in gh) == hlist, gname
+
+
+def test_theta_infinite_no_hard_part_lists_are_root_only():
+    # theta -> infinity: r_b -> delta. Unit masses on the eight corners of the unit cube: the root's centre of
+    # mass is its geometric centre (delta = 0) and every particle is b_max = sqrt(3)/2 from it. With R2 = 0 the
+    # R2 + b_max test is r >= b_max, met with equality by every one-particle group, so each group's list is the
+    # root cell alone (its own particle included in the root's monopole).
+    c = np.array([[i >> 2 & 1, i >> 1 & 1, i & 1] for i in range(8)], dtype=np.float64)
+    for theta in (1e6, math.inf):
+        T = oracle.Tree(c[:, 0], c[:, 1], c[:, 2], np.ones(8), oracle.Params(theta=theta, n_leaf=1, n_crit=1))
+        assert T.ng == 8 and T.moments["delta"][0] == 0.0
+        for cells, plist, hlist in T.walk():
+            assert list(cells) == [0] and len(plist) == 0 and len(hlist) == 0
+        soft, hard = T.interactions()
+        assert (soft, hard) == (8, 0)
+    # a finite theta of 1 opens the root for every corner (r_b = 1 > sqrt(3)/2)
+    T = oracle.Tree(c[:, 0], c[:, 1], c[:, 2], np.ones(8), oracle.Params(theta=1.0, n_leaf=1, n_crit=1))
+    assert all(0 not in set(cells) for cells, _, _ in T.walk())
+
+
+def test_interaction_counts_closed_forms():
+    # the counter is |group| x (list length) summed over groups, a sink's pair with itself included: at
+    # theta = 0 every soft list is every particle (N^2); with R2 beyond the system's diameter every hard list is
+    # too, and with R2 = 0 there is no hard list
+    s = ics.plummer(700, 9)
+    n = 700
+    diam = 2.0 * np.sqrt(np.max(s["x"] ** 2 + s["y"] ** 2 + s["z"] ** 2)) + 1.0
+    T = oracle.Tree(s["x"], s["y"], s["z"], s["m"], oracle.Params(theta=0.0, R1=diam, R2=2 * diam, n_leaf=8,
+                                                                     n_crit=16))
+    assert T.interactions() == (n * n, n * n)
+    T = oracle.Tree(s["x"], s["y"], s["z"], s["m"], oracle.Params(theta=0.0, n_leaf=8, n_crit=16))
+    assert T.interactions() == (n * n, 0)
+    # theta > 0: the same sum from the lists themselves
+    T = oracle.Tree(s["x"], s["y"], s["z"], s["m"], oracle.Params(theta=0.7, R1=0.05, R2=0.1, n_leaf=8, n_crit=16))
+    lists = T.walk()
+    cnt = T.count[T.gnode]
+    want = (int(sum(c * (len(a) + len(b)) for c, (a, b, _) in zip(cnt, lists))),
+            int(sum(c * len(h) for c, (_, _, h) in zip(cnt, lists))))
+    assert T.interactions() == want and want[0] < n * n
+
+
 @pytest.mark.parametrize("R1,R2", [(0.0, 0.0), (0.05, 0.1), (0.2, 0.4), (0.0, 0.3)])
 def test_tree_theta_zero_equals_direct(R1, R2):
     # with theta = 0 every cell opens: soft + hard is the direct sum for any R1 < R2
