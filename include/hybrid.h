@@ -310,9 +310,10 @@ const char *hybrid_server_last_error(hybrid_server *srv);
  * Scratch is a fixed device array inside the library, sized for
  * n <= HYBRID_ENERGY_NOALLOC_MAX_N (256 KB of FP64 partial sums); larger n returns
  * HYBRID_ETOOLARGE before anything is enqueued. Its address is looked up once
- * per device, on the first call made with that device current: make a first
- * call (n = 0 is enough: it only does this set-up and returns zeros) before
- * any stream capture. The scratch is shared by all calls on a device, so
+ * per device, on the first call made with that device current, which also
+ * loads the call's two kernels (so that a lazily loaded module does not take
+ * device memory at a later call): make a first call (n = 0 is enough: it only
+ * does this set-up and returns zeros) before any stream capture. The scratch is shared by all calls on a device, so
  * calls that overlap in time (two streams or two host threads) race on it and
  * must be serialised by the caller. Nothing in the scratch has to start at
  * zero: each call writes every slot it reads.

@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(ES_THREADS) k_energy_total(int64_t ntiles, dou
 }
 
 // Scratch address on the current device, looked up on the first call there.
+// The same set-up queries both kernels' attributes, which loads them: under
+// lazy module loading a kernel is otherwise loaded (and its code given device
+// memory) at its first launch, which an allocation-free caller cannot afford.
 cudaError_t scratch_for_current(double **out)
 {
     int dev = 0;
@@ -139,6 +142,10 @@ cudaError_t scratch_for_current(double **out)
     if (!g_scratch[dev]) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, es_scratch);
+        if (e != cudaSuccess) return e;
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, k_energy_tiles);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_energy_total);
         if (e != cudaSuccess) return e;
         g_scratch[dev] = (double *)p;
     }

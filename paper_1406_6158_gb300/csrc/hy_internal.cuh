@@ -91,7 +91,7 @@ struct WorkItem {
 };
 static_assert(sizeof(WorkItem) == 40, "WorkItem layout");
 constexpr uint32_t ITEM_MULTI = 0x80000000u;
-constexpr int LCH_FAR = 512, LCH_NEAR = 512, LCH_NEAR_SMALL = 64;
+constexpr int LCH_FAR = 2048, LCH_FAR_SMALL = 256, LCH_NEAR = 512, LCH_NEAR_SMALL = 64;
 
 // Entries per work item of a group of n sinks: lch for n >= 64, longer runs
 // (up to 8 lch) for smaller groups, so that items cost about the same
@@ -245,6 +245,8 @@ void launch_pair_far(hybrid_ctx *c);
 // near particles of the last walk: mode bit 0 adds F (1 - K) to the soft
 // accelerations (after launch_pair_far), bit 1 writes F K as the hard ones
 void launch_pair_near(hybrid_ctx *c, int mode);
+// shared-memory attributes of the far kernels (once per device, before any launch or capture)
+cudaError_t init_pair_kernels();
 
 // ---- integrator and io (integrate.cu) ----
 void launch_copy_in(hybrid_ctx *c, const SysIO *d_io, bool with_acc);

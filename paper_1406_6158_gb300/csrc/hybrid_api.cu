@@ -749,6 +749,7 @@ hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stre
     c->st = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e == cudaSuccess) e = init_pair_kernels();
     if (e != cudaSuccess) {
         delete c;
         return HYBRID_ECUDA;

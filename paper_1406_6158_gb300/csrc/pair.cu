@@ -893,6 +893,36 @@ void launch_pairs(hybrid_ctx *c, bool near, int mode)
 }  // namespace
 
 void launch_pair_far(hybrid_ctx *c) { launch_pairs(c, false, 1); }
+
+namespace {
+template <int KS, bool NEAR, bool SOFT, bool HARD, int NST>
+cudaError_t prefer_shared()
+{
+    return cudaFuncSetAttribute(k_pair_f32<KS, NEAR, SOFT, HARD, NST>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                (int)cudaSharedmemCarveoutMaxShared);
+}
+}  // namespace
+
+// The pair kernels are limited by registers and by shared memory per block:
+// the whole carveout goes to shared memory (they read nothing through L1
+// twice), so shared memory never limits their blocks per SM below registers.
+cudaError_t init_pair_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {prefer_shared<1, false, true, false, 2>(), prefer_shared<1, false, true, false, 3>(),
+                          prefer_shared<1, false, true, false, 4>(), prefer_shared<2, false, true, false, 2>(),
+                          prefer_shared<2, false, true, false, 3>(), prefer_shared<2, false, true, false, 4>(),
+                          prefer_shared<4, false, true, false, 2>(), prefer_shared<4, false, true, false, 3>(),
+                          prefer_shared<4, false, true, false, 4>(), prefer_shared<8, false, true, false, 2>(),
+                          prefer_shared<8, false, true, false, 3>(), prefer_shared<8, false, true, false, 4>(),
+                          prefer_shared<1, true, true, true, 3>(), prefer_shared<2, true, true, true, 3>(),
+                          prefer_shared<4, true, true, true, 3>(), prefer_shared<1, true, true, false, 3>(),
+                          prefer_shared<2, true, true, false, 3>(), prefer_shared<4, true, true, false, 3>(),
+                          prefer_shared<1, true, false, true, 3>(), prefer_shared<2, true, false, true, 3>(),
+                          prefer_shared<4, true, false, true, 3>()})
+        if (e == cudaSuccess) e = r;
+    return e;
+}
 void launch_pair_near(hybrid_ctx *c, int mode) { launch_pairs(c, true, mode); }
 
 }  // namespace hy

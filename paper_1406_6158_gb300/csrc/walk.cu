@@ -61,7 +61,7 @@ struct WalkArgs {
     unsigned long long *item_count;      // [0] far items, [1] near items
     WorkItem *items_far, *items_near;
     int64_t cap_items;
-    int lch_near;                        // base length of near work items
+    int lch_far, lch_near;               // base lengths of far and near work items
 };
 
 constexpr uint32_t WALK_REGION = 2048;
@@ -269,7 +269,7 @@ __device__ __forceinline__ bool emit_items(const WalkArgs &a, int t, uint64_t st
                                            uint32_t n, uint32_t sys, bool multi, int lane)
 {
     const int cls = t == 2 ? 1 : 0;
-    const uint64_t per = item_len(n, t == 2 ? a.lch_near : LCH_FAR);
+    const uint64_t per = item_len(n, t == 2 ? a.lch_near : a.lch_far);
     const uint64_t m = (len + per - 1) / per;
     unsigned long long base = 0;
     if (lane == 0) base = atomicAdd(a.item_count + cls, (unsigned long long)m);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
                     fail_items = true;
                     return ~0ull;
                 }
-                const uint64_t per = item_len(gn, t == 2 ? a.lch_near : LCH_FAR);
+                const uint64_t per = item_len(gn, t == 2 ? a.lch_near : a.lch_far);
                 (t == 2 ? early_near : early_far) += (uint32_t)((len + per - 1) / per);
             }
             const uint64_t size = tot > WALK_REGION ? tot : WALK_REGION;
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
         for (int t = 0; t < 3; ++t) {
             len3[t] = __shfl_sync(0xffffffffu, my_len, t);
             st3[t] = __shfl_sync(0xffffffffu, my_start, t);
-            const uint64_t per = item_len(gn, t == 2 ? a.lch_near : LCH_FAR);
+            const uint64_t per = item_len(gn, t == 2 ? a.lch_near : a.lch_far);
             (t == 2 ? fin_near : fin_far) += (uint32_t)((len3[t] + per - 1) / per);
         }
 #pragma unroll
@@ -534,8 +534,12 @@ void launch_walk(hybrid_ctx *c, int mode)
     a.items_near = (WorkItem *)c->wnear.p;
     a.cap_items = c->capWork;
     // near items: the near kernel's time per tile is mostly latency, so short items spread a small job over more
-    // warps; on large jobs every warp has items anyway and longer ones save the per-item set-up
-    a.lch_near = c->N <= (int64_t)1 << 20 ? LCH_NEAR_SMALL : LCH_NEAR;
+    // warps; on large jobs every warp has items anyway and longer ones save the per-item set-up. Far items: on a
+    // small job short items even out the warps' ends; on a large job long ones hide the set-up of each item (its
+    // descriptor, sinks and first gathers) behind more tiles
+    const bool small_job = c->N <= (int64_t)1 << 20;
+    a.lch_near = small_job ? LCH_NEAR_SMALL : LCH_NEAR;
+    a.lch_far = small_job ? LCH_FAR_SMALL : LCH_FAR;
     const int grid = c->walk_warps * 32 / WALK_THREADS;
     cudaEvent_t e0 = nullptr;
     prof_begin(c, PROF_WALK, &e0);

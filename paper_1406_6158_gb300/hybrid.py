@@ -192,16 +192,24 @@ class System:
 
 def hybrid_energy_noalloc(x, y, z, vx, vy, vz, m, G: float, eps: float, stream=None):
     """Kinetic and potential energy of one system through the allocation-free
-    entry point. Arrays are contiguous FP64 device tensors of one length;
-    `stream` is a torch.cuda.Stream or None (legacy default stream). Raises
-    HybridError on a non-OK status (ETOOLARGE above ENERGY_NOALLOC_MAX_N)."""
-    L = load()
+    entry point. Arrays are contiguous FP64 tensors of one length on the
+    current CUDA device (anything else raises ValueError before the C call:
+    the kernels read n doubles through each pointer); `stream` is a
+    torch.cuda.Stream or None (torch's current stream). Raises HybridError on
+    a non-OK status (ETOOLARGE above ENERGY_NOALLOC_MAX_N)."""
+    import torch
     n = int(x.numel())
-    for t in (x, y, z, vx, vy, vz, m):
-        if t.numel() != n or not t.is_contiguous():
-            raise ValueError("arrays must be contiguous and of one length")
+    arrays = (x, y, z, vx, vy, vz, m)
+    if any(t.numel() != n or not t.is_contiguous() for t in arrays):
+        raise ValueError("arrays must be contiguous and of one length")
+    for t in arrays:
+        if t.dtype != torch.float64:
+            raise ValueError("arrays must be float64, got %s" % t.dtype)
+        if not t.is_cuda or t.device.index != torch.cuda.current_device():
+            raise ValueError("arrays must be on the current CUDA device, got %s" % t.device)
+    L = load()
     T, W = C.c_double(), C.c_double()
-    st = None if stream is None else stream.cuda_stream
+    st = (torch.cuda.current_stream() if stream is None else stream).cuda_stream
     code = L.hybrid_energy_noalloc(n, *[_ptr(t) for t in (x, y, z, vx, vy, vz, m)], float(G), float(eps), st,
                                    C.byref(T), C.byref(W))
     if code != OK:

@@ -100,3 +100,22 @@ def test_system_fields_match_header():
         fields += [f.strip().lstrip("*") for f in names.split(",")]
     assert fields == [f for f, _ in hybrid.hybrid_system._fields_]
 
+
+
+def test_noalloc_binding_refuses_foreign_tensors_before_the_call(monkeypatch):
+    # the kernels read n doubles through each pointer: float32, CPU or mismatched tensors must never reach them
+    torch = pytest.importorskip("torch")
+    from paper_1406_6158_gb300 import hybrid
+
+    def no_load():
+        raise AssertionError("the library was reached")
+
+    monkeypatch.setattr(hybrid, "load", no_load)
+    f64 = [torch.zeros(8, dtype=torch.float64) for _ in range(7)]
+    with pytest.raises(ValueError, match="CUDA device"):
+        hybrid.hybrid_energy_noalloc(*f64, 1.0, 0.01)
+    f32 = [torch.zeros(8, dtype=torch.float32) for _ in range(7)]
+    with pytest.raises(ValueError, match="float64"):
+        hybrid.hybrid_energy_noalloc(*f32, 1.0, 0.01)
+    with pytest.raises(ValueError, match="one length"):
+        hybrid.hybrid_energy_noalloc(*f64[:6], torch.zeros(9, dtype=torch.float64), 1.0, 0.01)

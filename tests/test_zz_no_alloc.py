@@ -68,6 +68,21 @@ def test_noalloc_on_a_side_stream(H):
         assert abs(T - T0) <= RTOL * abs(T0) and abs(W - W0) <= RTOL * abs(W0)
 
 
+def test_noalloc_takes_no_device_memory(H):
+    # after a first call on the device (set-up: scratch address, kernels loaded), further calls leave the
+    # device's free memory and torch's reserved pool exactly where they were
+    st = ics.plummer(3001, seed=3)
+    _, _, s = _energy_ctx(H, st, 1.0, 0.02)
+    H.hybrid_energy_noalloc(*_args(s), 1.0, 0.02)
+    torch.cuda.synchronize()
+    free0, reserved0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_reserved()
+    for _ in range(2):
+        H.hybrid_energy_noalloc(*_args(s), 1.0, 0.02)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.cuda.memory_reserved() == reserved0
+
+
 def test_noalloc_limits(H):
     L = H.load()
     T, W = C.c_double(7.0), C.c_double(7.0)
