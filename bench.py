@@ -13,9 +13,12 @@ kernels on FP64 state. Prints one JSON line.
 path has no exchange step, so there is no collective on the data path.
 --impl reference times the CPU FP64 oracle on the host cores instead.
 Beside the headline the line carries the same workload with reused trees and
-neighbour lists (a Verlet skin; not the paper's scheme). Other workloads:
---workload large | batched | served | paper (hybrid against normal tree with
-the paper's parameter set).
+neighbour lists (a Verlet skin; not the paper's scheme) and two compact
+sub-records measured in the same run: "large" (one Hernquist sphere of 2^24
+particles, theta = 0.4, n_hard = 8) and "batched" (512 Plummer spheres of
+uneven N in one call per step, against the same systems one per call in
+FP64). Each workload also runs alone: --workload large | batched | served |
+paper (hybrid against normal tree with the paper's parameter set).
 """
 from __future__ import annotations
 
@@ -34,10 +37,11 @@ sys.path.insert(0, ROOT)
 N_DEFAULT = 1 << 17
 METRIC = "particle-steps/s"
 FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul, 3 fma (by convention 20)
-# DRAM bytes (read + write) of one far-pair launch on this workload, from ncu captures of the kernel
-# variants the keys name (n_crit, threads per group, staging depth); see profiles/far_pair_plummer131k.md.
-# Reported as the roofline's traffic only when the autotuner picks one of these variants.
-FAR_TRAFFIC_BYTES = {(128, 16, 0): 57.009e6, (128, 32, 2): 56.80e6, (128, 32, 4): 56.78e6}
+# DRAM bytes (read + write) of one far-pair launch on this workload, from one ncu capture of the current far
+# kernel for each variant the keys name (n_crit, threads per group, staging depth). Reported as the roofline's
+# traffic only when the autotuner picks one of these variants, else None.
+FAR_TRAFFIC_BYTES = {}
+CLOCK_INTERVAL_MS = 20
 L2_FLUSH_BYTES = 256 << 20
 ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
 # Verlet skin of the reused-list measurement: twice the distance the fastest particle of the Plummer sphere
@@ -106,13 +110,13 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(CLOCK_INTERVAL_MS)],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0, "interval_ms": CLOCK_INTERVAL_MS}
         if self.proc is None:
             return out
         self.proc.terminate()
@@ -219,14 +223,17 @@ def c4_systems(count=512, seed=3):
     return out
 
 
-def run_c4(args):
+C4_NAME = ("batched ensemble: %d Plummer spheres, N log-uniform in [2^10, 2^17] (seed 3), total N=%d, "
+           "eps=1/(4 N^(1/3)), theta=0.5, R1=4eps, R2=8eps, dt_s=1/128, n_hard=4; one call per step for all "
+           "systems (CUDA graph), FP32 pairs, FP64 state")
+
+
+def c4_record(args, steps, warmup):
     """Batched FP32 form (one call advances all systems; autotuned n_crit, threads per group, staging depth)
     against the plain form (FP64, one system per call), same systems, one soft step each."""
     import numpy as np
     import torch
-    from paper_1406_6158_gb300 import build as cuda_build
     from paper_1406_6158_gb300 import hybrid, ics
-    cuda_build.build()
     specs = c4_systems(args.c4_count)
     total = sum(n for n, _, _ in specs)
     states = [ics.plummer(n, sd) for n, sd, _ in specs]
@@ -242,15 +249,15 @@ def run_c4(args):
     sysb = [hybrid.System(st, precision=1, ids=False, params=per(1, kw)) for st, (_, _, kw) in zip(states, specs)]
     chosen, table = ctx.hybrid_autotune(sysb)
     ctx.hybrid_step_batched(sysb, 0)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         ctx.hybrid_step_batched(sysb, 1)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    clocks = ClockSampler(0)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     launches0 = ctx.hybrid_launch_count()
     torch.cuda.synchronize()
     clocks.start()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
         ctx.hybrid_step_batched(sysb, 1)
@@ -259,19 +266,22 @@ def run_c4(args):
     clk = clocks.stop()
     launches = ctx.hybrid_launch_count() - launches0
     t_b = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    v_b = total * args.steps / t_b
+    v_b = total * steps / t_b
     # ---- plain FP64, one system per call ----
     ctx64 = hybrid.Context(per(0, specs[0][2]), stream)
     sys64 = [hybrid.System(st, precision=0, ids=False, params=per(0, kw)) for st, (_, _, kw) in zip(states, specs)]
     for s in sys64:
         ctx64.hybrid_step(s, 0)
     torch.cuda.synchronize()
+    clocks64 = ClockSampler(torch.cuda.current_device())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks64.start()
     e0.record(stream)
     for s in sys64:
         ctx64.hybrid_step(s, 1)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk64 = clocks64.stop()
     t_p = e0.elapsed_time(e1) / 1e3
     v_p = total / t_p
     # ---- force error against direct summation on a few systems ----
@@ -284,26 +294,37 @@ def run_c4(args):
             a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
             a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
             errs[name].append(force_error_rms(out, a_s, a_h, specs[k][2]["eps"], nsample=256))
-    line = {
-        "metric": METRIC, "value": v_b, "unit": METRIC, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "batched ensemble: %d Plummer spheres, N log-uniform in [2^10, 2^17] (seed 3), "
-                               "total N=%d, eps=1/(4 N^(1/3)), theta=0.5, R1=4eps, R2=8eps, dt_s=1/128, n_hard=4; "
-                               "one call per step for all systems (CUDA graph), FP32 pairs, FP64 state"
-                               % (len(specs), total),
-                   "N_total": total, "systems": len(specs), "l2": "flushed (256 MiB write) before every timed step"},
+    ctx.close()
+    ctx64.close()
+    del sysb, sys64, flush
+    torch.cuda.empty_cache()
+    return {
+        "workload": C4_NAME % (len(specs), total), "N_total": total, "systems": len(specs),
+        "metric": METRIC, "value": v_b, "unit": METRIC, "steps": steps, "warmup": warmup,
+        "ms_per_step": 1e3 * t_b / steps, "dtype": "f32", "l2": "flushed (256 MiB write) before every timed step",
         "autotune": {"chosen": {"n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]},
                      "est_ms_per_step": [round(float(x), 3) for x in table]},
-        "plain_fp64": {"value": v_p, "unit": METRIC, "ms_per_step": 1e3 * t_p,
+        "plain_fp64": {"value": v_p, "unit": METRIC, "ms_per_step": 1e3 * t_p, "clocks": clk64,
                        "form": "FP64 pairs, one system per hybrid_step call, same systems"},
         "batched_over_plain": v_b / v_p,
         "force_err_rms_vs_direct": {k: float(np.mean(v)) for k, v in errs.items()},
         "gpu_launches": launches, "clocks": clk,
     }
+
+
+def run_c4(args):
+    from paper_1406_6158_gb300 import build as cuda_build
+    cuda_build.build()
+    r = c4_record(args, args.steps, args.warmup)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": 1, "steps": r["steps"],
+        "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "N_total": r["N_total"], "systems": r["systems"], "l2": r["l2"]},
+    }
+    line.update({k: r[k] for k in ("autotune", "plain_fp64", "batched_over_plain", "force_err_rms_vs_direct",
+                                   "gpu_launches", "clocks")})
     print(json.dumps(line), flush=True)
-    ctx.close()
-    ctx64.close()
     return 0
 
 
@@ -424,31 +445,72 @@ def run_c5(args):
     return 0
 
 
-def hbm_stages(n, n_hard, ms):
+def hbm_stages(n, n_hard, ms, nodes=None):
     """Achieved HBM bandwidth of the memory-bound stages from their live times per soft step and their
-    algorithmic bytes per particle: key sort per build 36 (keys: x, y, z in, key and index out) + 8 (digit
-    counts) + 8 passes x 24 (key and index in and out); kick + drift 108 per drift launch (v 24, a 12, x 24 in;
-    v 24, x 24 out). n_hard builds and drift launches per soft step."""
+    algorithmic bytes (n_hard builds and drift launches per soft step):
+      sort        per particle 36 (keys: x, y, z in, key and index out) + 8 (digit counts) + 8 passes x 24
+                  (key and index in and out)
+      topology    per particle 8 (sorted key in); per node 24 out (first, count, level, first child, children,
+                  parent)
+      moments     per particle 32 (FP32 hi/lo position copies in); per node 24 in (the topology) and 72 out (the
+                  walk's and pair kernels' records: centre of mass and mass hi/lo, lo and B2, opening and
+                  neighbour radii, topology)
+      kick_drift  per particle 108 (v 24, a 12, x 24 in; v 24, x 24 out)
+    nodes: tree nodes of one build (topology and moments are reported only when it is given)."""
     peak = float(measured_peaks().get("hbm_gbs", 6655.6))
+    per = {"sort": (36 + 8 + 8 * 24, 0), "kick_drift": (108, 0)}
+    if nodes:
+        per["topology"] = (8, 24)
+        per["moments"] = (32, 24 + 72)
     out = {}
-    for name, per_particle in (("sort", 36 + 8 + 8 * 24), ("kick_drift", 108)):
+    for name, (pp, pn) in per.items():
         t = ms.get(name)
         if not t:
             continue
-        gbs = n * per_particle * n_hard / (t / 1e3) / 1e9
-        out[name] = {"bytes_per_particle_per_launch": per_particle, "launches_per_step": n_hard, "GB/s": gbs,
-                     "frac_of_measured_hbm": gbs / peak}
+        launch_bytes = n * pp + (nodes or 0) * pn
+        gbs = launch_bytes * n_hard / (t / 1e3) / 1e9
+        out[name] = {"bytes_per_launch": launch_bytes, "bytes_per_particle": pp, "bytes_per_node": pn,
+                     "launches_per_step": n_hard, "GB/s": gbs, "frac_of_measured_hbm": gbs / peak}
     return out
 
 
-def run_c3(args):
+C3_NAME = ("Hernquist sphere N=%d seed 2, a=1, r<=100, eps=1/512, theta=0.4, R1=3eps, R2=6eps, dt_s=1/128, "
+           "n_hard=8; FP32 pairs, FP64 state")
+
+
+def c3_cpu_leg(st, P, ngroups_sample=64):
+    """The oracle on the host's cores for the large workload, sampled: one whole tree build (timed) and the
+    soft and hard forces of sampled groups (timed), scaled to one soft step (n_hard builds, one soft and n_hard
+    hard force evaluations over all groups)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    op = oracle.Params(G=P.G, eps=P.eps, theta=P.theta, R1=P.R1, R2=P.R2, dt_soft=P.dt_soft, a_err=P.a_err,
+                       n_hard=P.n_hard, n_leaf=P.n_leaf, n_crit=P.n_crit, mac=P.mac)
+    t0 = time.perf_counter()
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], op)
+    t_build = time.perf_counter() - t0
+    sel = np.sort(np.random.default_rng(5).choice(T.ng, min(ngroups_sample, T.ng), replace=False))
+    t0 = time.perf_counter()
+    T.forces(groups=sel, mode=1)
+    t_soft = (time.perf_counter() - t0) * T.ng / len(sel)
+    t0 = time.perf_counter()
+    T.forces(groups=sel, mode=2)
+    t_hard = (time.perf_counter() - t0) * T.ng / len(sel)
+    step = P.n_hard * t_build + t_soft + P.n_hard * t_hard
+    n = len(st["x"])
+    return {"value": n / step, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "one tree build of all %d particles (%.1f s) and the soft and hard forces of %d of %d groups, "
+                      "scaled to one soft step = %d builds + 1 soft + %d hard evaluations over all groups "
+                      "(%.0f s estimated)" % (n, t_build, len(sel), T.ng, P.n_hard, P.n_hard, step)}
+
+
+def c3_record(args, steps, warmup, with_cpu=True):
     """Large single system: Hernquist sphere N=2^24 (seed 2, a=1, r<=100), eps=1/512, theta=0.4, R1=3eps,
     R2=6eps, dt_s=1/128, n_hard=8, FP32 pairs on FP64 state."""
     import numpy as np
     import torch
-    from paper_1406_6158_gb300 import build as cuda_build
     from paper_1406_6158_gb300 import hybrid, ics
-    cuda_build.build()
     n = args.n if args.n != N_DEFAULT else 1 << 24
     eps = 1.0 / 512
     tic = time.perf_counter()
@@ -463,18 +525,20 @@ def run_c3(args):
     chosen, _ = ctx.hybrid_autotune(s, [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0),
                                          (256, 64, 2), (256, 32, 0)])
     ctx.hybrid_step(s, 0)
-    for _ in range(args.warmup):
+    nodes, groups = ctx.tree_info()
+    for _ in range(warmup):
         ctx.hybrid_step(s, 1)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     ctx.hybrid_profile(True)
     for k in range(9):
         ctx.hybrid_profile_read(k, reset=True)
     launches0 = ctx.hybrid_launch_count()
-    clocks = ClockSampler(0)
+    fallbacks0 = ctx.hybrid_sort_fallbacks()
+    clocks = ClockSampler(torch.cuda.current_device())
     inter_far = inter_near = 0
     torch.cuda.synchronize()
     clocks.start()
-    for k in range(args.steps):
+    for k in range(steps):
         ev[k][0].record(stream)
         ctx.hybrid_step(s, 1)
         ev[k][1].record(stream)
@@ -484,39 +548,62 @@ def run_c3(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = ctx.hybrid_launch_count() - launches0
-    t = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    fallbacks = ctx.hybrid_sort_fallbacks() - fallbacks0
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t = sum(per_step) / 1e3
     kinds = [ctx.hybrid_profile_read(k) for k in range(9)]
     ctx.hybrid_profile(False)
-    props = torch.cuda.get_device_properties(0)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
     sm_max = float(measured_peaks().get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, sm_max)
     far_s = kinds[0][0] / 1e3 / max(kinds[0][1], 1)
-    achieved = FLOPS_PER_INTERACTION * inter_far / args.steps / far_s / 1e12
+    achieved = FLOPS_PER_INTERACTION * inter_far / steps / far_s / 1e12
     out = s.numpy()
     a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
     a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
     ferr = force_error_rms(out, a_s, a_h, eps, nsample=256)
     names = ["far_pair", "near_pair", "walk", "tree_build", "kick_drift", "sort", "topology", "moments", "groups"]
-    line = {
-        "metric": METRIC, "value": n * args.steps / t, "unit": METRIC, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "Hernquist sphere N=%d seed 2, a=1, r<=100, eps=1/512, theta=0.4, R1=3eps, "
-                               "R2=6eps, dt_s=1/128, n_hard=8; FP32 pairs, FP64 state" % n,
-                   "N": n, "l2": "inputs larger than L2", "ic_seconds": t_ic,
-                   "autotuned": {"n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]}},
-        "interactions_per_s": (inter_far + P.n_hard * inter_near) / t,
-        "soft_interactions_per_step": (inter_far + inter_near) / args.steps,
-        "hard_interactions_per_substep": inter_near / args.steps,
-        "force_err_rms_vs_direct": ferr,
-        "kernel_ms_per_step": {nm: kinds[k][0] / args.steps for k, nm in enumerate(names)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_pair_f32 far (cells + far particles, soft force)"},
-        "hbm_stages": hbm_stages(n, P.n_hard, {nm: kinds[k][0] / args.steps for k, nm in enumerate(names)}),
-        "gpu_launches": launches, "clocks": clk,
-    }
-    print(json.dumps(line), flush=True)
+    ms = {nm: kinds[k][0] / steps for k, nm in enumerate(names)}
     ctx.close()
+    del s, out, a_s, a_h
+    torch.cuda.empty_cache()
+    cpu = c3_cpu_leg(st, P) if with_cpu else None
+    return {
+        "workload": C3_NAME % n, "N": n, "metric": METRIC, "value": n * steps / t, "unit": METRIC, "steps": steps,
+        "warmup": warmup, "ms_per_step": 1e3 * t / steps, "ms_median": sorted(per_step)[len(per_step) // 2],
+        "ms_max": max(per_step), "dtype": "f32", "l2": "inputs larger than L2", "ic_seconds": t_ic,
+        "autotuned": {"n_crit": chosen[0], "threads_per_group": chosen[1], "tile_depth": chosen[2]},
+        "nodes": nodes, "groups": groups,
+        "interactions_per_s": (inter_far + P.n_hard * inter_near) / t,
+        "soft_interactions_per_step": (inter_far + inter_near) / steps,
+        "hard_interactions_per_substep": inter_near / steps,
+        "force_err_rms_vs_direct": ferr,
+        "kernel_ms_per_step": ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "k_pair_f32 far (cells + far particles, soft force)",
+                     "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
+                                  (props.multi_processor_count, sm_max)},
+        "hbm_stages": hbm_stages(n, P.n_hard, ms, nodes),
+        "gpu_launches": launches, "sort_fallbacks": fallbacks, "clocks": clk, "cpu_baseline": cpu,
+    }
+
+
+def run_c3(args):
+    from paper_1406_6158_gb300 import build as cuda_build
+    cuda_build.build()
+    r = c3_record(args, args.steps, args.warmup, with_cpu=not args.no_cpu_baseline)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": 1, "steps": r["steps"],
+        "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "N": r["N"], "l2": r["l2"], "ic_seconds": r["ic_seconds"],
+                   "autotuned": r["autotuned"]},
+    }
+    line.update({k: r[k] for k in ("interactions_per_s", "soft_interactions_per_step", "hard_interactions_per_substep",
+                                   "force_err_rms_vs_direct", "kernel_ms_per_step", "roofline", "hbm_stages",
+                                   "gpu_launches", "sort_fallbacks", "clocks", "cpu_baseline", "ms_median", "ms_max",
+                                   "nodes", "groups")})
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -649,6 +736,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-reuse", action="store_true", help="skip the reused-neighbour-list measurement")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the compact large and batched records of the default run")
     ap.add_argument("--ref-max-seconds", type=float, default=120.0,
                     help="time box of the reference arm's timed steps (the oracle on the host cores)")
     ap.add_argument("--traffic-bytes", type=float, default=None,
@@ -724,6 +813,7 @@ def main():
     for k in range(9):
         ctx.hybrid_profile_read(k, reset=True)
     launches0 = ctx.hybrid_launch_count()
+    fallbacks0 = ctx.hybrid_sort_fallbacks()
     inter_far = inter_near = 0
     barrier()
     clocks.start()
@@ -738,7 +828,10 @@ def main():
     barrier()
     clk = clocks.stop()
     launches = ctx.hybrid_launch_count() - launches0
-    t_steps = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    fallbacks = ctx.hybrid_sort_fallbacks() - fallbacks0
+    per_step = [a.elapsed_time(b) for a, b in ev]
+    t_steps = sum(per_step) / 1e3
+    nodes, groups = ctx.tree_info()            # the tree of the last timed build
     soft_ms, soft_n = ctx.hybrid_profile_read(0)
     hard_ms, hard_n = ctx.hybrid_profile_read(1)
     ctx.hybrid_profile_read(0, reset=True)     # a reset clears every kind
@@ -817,6 +910,10 @@ def main():
         e2e = {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                "steps": ke}
 
+    out = s.numpy()
+    a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
+    a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
+
     # ---- roofline of the dominant kernel (soft pair, FP32 CUDA-core bound) ----
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
@@ -832,11 +929,24 @@ def main():
                 "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
                              (props.multi_processor_count, sm_max)}
 
+    ctx.close()
+
+    # ---- compact records of the large and the batched workloads (one GPU) ----
+    subs = {}
+    if ws == 1 and not args.no_sub:
+        import gc
+        del s
+        gc.collect()
+        torch.cuda.empty_cache()
+        large_steps = max(2, min(args.steps, 4))
+        subs["large"] = c3_record(args, large_steps, 2, with_cpu=not args.no_cpu_baseline)
+        gc.collect()
+        torch.cuda.empty_cache()
+        subs["batched"] = c4_record(args, max(3, min(args.steps, 5)), 3)
+        torch.cuda.set_stream(stream)
+
     line = None
     if rank == 0:
-        out = s.numpy()
-        a_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)
-        a_h = np.stack([out["ax_h"], out["ay_h"], out["az_h"]], 1).astype(np.float64)
         ferr = force_error_rms(out, a_s, a_h, w["eps"])
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
@@ -844,7 +954,8 @@ def main():
         step_ms = 1e3 * t_steps / args.steps
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_ms, "ms_median": sorted(per_step)[len(per_step) // 2],
+            "ms_max": max(per_step), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(w), "N": w["n"], "parallelism": "replicas x%d" % ws,
                        "l2": "flushed (256 MiB write) before every timed step", "state": "f64",
@@ -868,10 +979,14 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
+            "sort_fallbacks": fallbacks,
             "clocks": clk,
+            "tree": {"nodes": nodes, "groups": groups},
+            "hbm_stages": hbm_stages(w["n"], w["n_hard"], {"sort": stage[5], "topology": stage[6],
+                                                           "moments": stage[7], "kick_drift": stage[4]}, nodes),
         }
+        line.update(subs)
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()

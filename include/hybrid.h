@@ -244,6 +244,14 @@ hybrid_status hybrid_profile_read(hybrid_ctx *ctx, int kind, double *ms, int64_t
 /* Number of kernels this context has launched so far (all kinds). */
 int64_t hybrid_launch_count(hybrid_ctx *ctx);
 
+/* Number of tree builds this context has repeated with the radix sort. The
+ * key sort of Sec. III-A1 is first tried as a sample sort, which assumes the
+ * state is close to key order (as it is from one build to the next: the state
+ * stays in key order and moves by one drift); when a bucket overflows, the
+ * build leaves the order unchanged and is repeated with the radix sort. Both
+ * give the same stable order. A diagnostic; not part of the method. */
+int64_t hybrid_sort_fallbacks(hybrid_ctx *ctx);
+
 /* Softened energies (Sec. IV-A "total energy") of a system by direct
  * summation on the device: kinetic and potential, returned to the host
  * (synchronises). Uses the context's eps and G (or sys->params). */

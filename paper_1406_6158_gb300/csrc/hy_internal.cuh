@@ -60,6 +60,22 @@ __device__ __forceinline__ void grid_split(double x, double lo0, const SysBox &b
 // Internal status code (never returned to the caller): a particle moved more
 // than skin / 2 since the last build; the step resumes with a rebuild.
 constexpr int32_t ST_SKIN = 100;
+// Internal status code: a bucket of the sample sort held more keys than a
+// block sorts in shared memory; the build left the order unchanged and is
+// repeated with the radix sort.
+constexpr int32_t ST_SORT = 101;
+
+// Sample sort of the keys (the usual path once the state is close to key
+// order): per system, nb buckets of about SS_BUCKET keys split by keys taken
+// at regular positions; a bucket of at most SS_CAP keys is sorted in one block
+// (4 times the target: a particle that moved far in the order shifts the
+// splitters around it by up to one bucket).
+constexpr int SS_BUCKET = 2048;
+constexpr int SS_CAP = 8192;
+struct SSys {
+    int32_t nb;      // buckets of the system
+    int32_t bbase;   // index of its first bucket
+};
 
 // Device status block: first failure wins (atomicCAS on code).
 struct Status {
@@ -147,6 +163,12 @@ struct hybrid_ctx {
     std::vector<hy::SysIO> h_io;
     int nchunks = 0;
     int ipt = hy::RS_IPT_MAX, tile = hy::RS_TILE_MAX;   // radix tile: 8 warps x 32 lanes x ipt keys, sized to fill the GPU
+    // sample sort layout of the batch (buckets over all systems) and whether the current call repeats a build
+    // with the radix sort after a bucket overflowed
+    std::vector<hy::SSys> h_ss;
+    int nbk = 0;
+    bool ss_ok = false, sort_fallback = false;
+    int64_t sort_fallbacks = 0;
     bool tree_valid = false, have_soft = false, have_hard = false;
     // reused neighbour lists (skin > 0): the lists of the last walk still hold for the working state of the
     // batch with this signature (set at the end of a step, cleared by anything else that builds or walks)
@@ -163,6 +185,8 @@ struct hybrid_ctx {
     hy::Buf phi, plo, pd;                  // float4 hi/lo (precision 1), double4_32a (precision 0)
     hy::Buf disp;                          // float: bound of the distance moved since the last build (skin > 0)
     hy::Buf keys[2], vals[2], hist, blocksum;
+    hy::Buf ss_sys, ss_spk, ss_spv, ss_cnt, ss_start, ss_cur, ss_pb, ss_flag;   // sample sort
+    int64_t capBk = 0;
     hy::Buf off_dev, sp_dev, chunks_dev, boxmin, boxmax, box, sysroot;
     hy::Buf status;
     // tree
@@ -247,6 +271,8 @@ void launch_pair_far(hybrid_ctx *c);
 void launch_pair_near(hybrid_ctx *c, int mode);
 // shared-memory attributes of the far kernels (once per device, before any launch or capture)
 cudaError_t init_pair_kernels();
+// shared-memory attribute of the sample sort's splitter kernel
+cudaError_t init_tree_kernels();
 
 // ---- integrator and io (integrate.cu) ----
 void launch_copy_in(hybrid_ctx *c, const SysIO *d_io, bool with_acc);

@@ -228,6 +228,15 @@ bool reserve(hybrid_ctx *c)
         ok = ok && ensure(c, c->chunks_dev, (size_t)c->nchunks * sizeof(Chunk));
         if (ok) c->capChunks = c->nchunks;
     }
+    // sample sort: a system table, splitters and bucket counts, starts and cursors, each key's bucket
+    ok = ok && ensure(c, c->ss_sys, (size_t)S * sizeof(SSys)) && ensure(c, c->ss_flag, 256) &&
+         ensure(c, c->ss_pb, (size_t)std::max<int64_t>(N, 1) * 4);
+    if (c->nbk > c->capBk) {
+        const size_t nb = (size_t)c->nbk;
+        ok = ok && ensure(c, c->ss_spk, nb * 8) && ensure(c, c->ss_spv, nb * 4) && ensure(c, c->ss_cnt, nb * 4) &&
+             ensure(c, c->ss_start, nb * 4) && ensure(c, c->ss_cur, nb * 4);
+        if (ok) c->capBk = c->nbk;
+    }
     // radix sort scratch: 64 tickets, digit counts [S][8][256], look-back words [8][chunks][256]
     ok = ok && ensure(c, c->hist, ((size_t)64 + (size_t)2048 * (S + c->nchunks)) * 4);
     if (c->capNodes < std::max<int64_t>(4096, N)) ok = ok && alloc_nodes(c, std::max<int64_t>(4096, N));
@@ -318,6 +327,17 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
         }
     }
     c->nchunks = (int)c->h_chunks.size();
+    // sample sort layout: about SS_BUCKET keys per bucket
+    c->h_ss.resize(S);
+    c->nbk = 0;
+    c->ss_ok = true;
+    for (int s = 0; s < S; ++s) {
+        const int64_t n = c->h_off[s + 1] - c->h_off[s];
+        SSys &y = c->h_ss[s];
+        y.nb = (int32_t)((n + SS_BUCKET - 1) / SS_BUCKET);
+        y.bbase = c->nbk;
+        c->nbk += y.nb;
+    }
     if (!reserve(c)) return HYBRID_ENOMEM;
     c->h_io.resize(S);
     for (int s = 0; s < S; ++s) {
@@ -345,7 +365,8 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
         (e = cudaMemcpyAsync(c->sp_dev.p, c->h_sp.data(), S * sizeof(SysParams), cudaMemcpyHostToDevice, c->st)) ||
         (e = cudaMemcpyAsync(c->chunks_dev.p, c->h_chunks.data(), c->nchunks * sizeof(Chunk),
                              cudaMemcpyHostToDevice, c->st)) ||
-        (e = cudaMemcpyAsync(c->io_dev.p, c->h_io.data(), S * sizeof(SysIO), cudaMemcpyHostToDevice, c->st)))
+        (e = cudaMemcpyAsync(c->io_dev.p, c->h_io.data(), S * sizeof(SysIO), cudaMemcpyHostToDevice, c->st)) ||
+        (e = cudaMemcpyAsync(c->ss_sys.p, c->h_ss.data(), S * sizeof(SSys), cudaMemcpyHostToDevice, c->st)))
         return cuda_fail(c, e, "upload of the batch tables");
     c->tree_valid = false;
     return HYBRID_OK;
@@ -477,6 +498,8 @@ uint64_t ops_signature(const hybrid_ctx *c, const std::vector<Op> &ops)
     mix((uint64_t)c->S);
     mix((uint64_t)c->nchunks);
     mix((uint64_t)c->ipt);
+    mix((uint64_t)c->nbk);
+    mix((uint64_t)c->ss_ok);
     mix((uint64_t)c->prof);
     for (const Op &o : ops) {
         mix((uint64_t)o.kind);
@@ -571,9 +594,14 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops_in)
     std::vector<Op> ops = ops_in;
     size_t start = 0;
     bool skin_recovered = false;
+    c->sort_fallback = false;
+    struct SortMode {   // the radix sort of a fallback lasts for this sequence only
+        hybrid_ctx *c;
+        ~SortMode() { c->sort_fallback = false; }
+    } sort_mode{c};
     for (int attempt = 0; attempt < 12; ++attempt) {
         std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> *gev = nullptr;
-        if (!(attempt == 0 && !skin_recovered && launch_as_graph(c, ops, &gev)))
+        if (!(attempt == 0 && !skin_recovered && !c->sort_fallback && launch_as_graph(c, ops, &gev)))
             for (size_t i = start; i < ops.size(); ++i) enqueue(c, ops[i], (int)i);
         cudaError_t le = cudaGetLastError();
         if (le != cudaSuccess) return cuda_fail(c, le, "kernel launch");
@@ -590,6 +618,17 @@ hybrid_status run_ops(hybrid_ctx *c, const std::vector<Op> &ops_in)
             c->ev_used.clear();
         }
         if (s.code == 0) return HYBRID_OK;
+        if (s.code == ST_SORT && !c->sort_fallback && s.where >= 0 && (size_t)s.where < ops.size()) {
+            // a sample-sort bucket overflowed (a state far from key order): that build left the order as it was
+            // and skipped the rest; repeat from it with the radix sort (eagerly; the captured graphs stay)
+            c->sort_fallback = true;
+            c->sort_fallbacks++;
+            start = (size_t)s.where;
+            while (start > 0 && ops[start].kind != OP_BUILD) --start;
+            --attempt;
+            if ((r = clear_status(c)) != HYBRID_OK) return r;
+            continue;
+        }
         drop_graphs(c);
         if (s.code == ST_SKIN && !skin_recovered && s.where >= 0 && (size_t)s.where < ops.size()) {
             // a particle moved more than skin / 2 in the drift of op `where`: that hard step and every later
@@ -750,6 +789,7 @@ hybrid_status hybrid_create(hybrid_ctx **out, const hybrid_params *p, void *stre
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->dev);
     if (e == cudaSuccess) e = init_pair_kernels();
+    if (e == cudaSuccess) e = init_tree_kernels();
     if (e != cudaSuccess) {
         delete c;
         return HYBRID_ECUDA;
@@ -796,6 +836,7 @@ hybrid_status hybrid_destroy(hybrid_ctx *c)
     else cudaDeviceSynchronize();
     Buf *all[] = {&c->id, &c->ida, &c->orig, &c->origa, &c->psys, &c->phi, &c->plo, &c->pd, &c->disp, &c->keys[0], &c->keys[1],
                   &c->vals[0], &c->vals[1], &c->hist, &c->blocksum, &c->off_dev, &c->sp_dev, &c->chunks_dev,
+                  &c->ss_sys, &c->ss_spk, &c->ss_spv, &c->ss_cnt, &c->ss_start, &c->ss_cur, &c->ss_pb, &c->ss_flag,
                   &c->boxmin, &c->boxmax, &c->box, &c->sysroot, &c->status, &c->lvl, &c->nfirst, &c->ncount,
                   &c->nchild, &c->nnch, &c->nparent, &c->nlevel, &c->ndone, &c->leafof, &c->pc, &c->pD, &c->pn, &c->rec,
                   &c->rb2d, &c->rd2b, &c->rhist, &c->nM, &c->ncx,
@@ -1235,6 +1276,8 @@ hybrid_status hybrid_profile_read(hybrid_ctx *c, int kind, double *ms, int64_t *
 }
 
 int64_t hybrid_launch_count(hybrid_ctx *c) { return c ? c->launches : 0; }
+
+int64_t hybrid_sort_fallbacks(hybrid_ctx *c) { return c ? c->sort_fallbacks : 0; }
 
 hybrid_status hybrid_energy(hybrid_ctx *c, hybrid_system *sys, double *kinetic, double *potential)
 {

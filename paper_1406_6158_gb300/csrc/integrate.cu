@@ -21,8 +21,9 @@ struct StatePtrs {
 
 __device__ __forceinline__ void fail(Status *st, int code, int where)
 {
-    atomicCAS(&st->code, 0, code);
-    st->where = where;
+    // the first failure wins and keeps its op index: later kernels of the same sequence may fail too (a build
+    // after an unsorted one), and the sequence resumes at the first
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
 // system of batch position i: binary search over the offsets (S + 1 entries)

@@ -19,8 +19,9 @@ namespace {
 
 __device__ __forceinline__ void fail(Status *st, int code, int where)
 {
-    atomicCAS(&st->code, 0, code);
-    st->where = where;
+    // the first failure wins and keeps its op index: later kernels of the same sequence may fail too (a build
+    // after an unsorted one), and the sequence resumes at the first
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
 // order-preserving map of doubles to unsigned integers (for atomic min/max)
@@ -357,6 +358,350 @@ __global__ void __launch_bounds__(256) k_onesweep(const uint64_t *__restrict__ k
                     vout[dst] = sval[lp];
                 }
             }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Sample sort of the keys, for a state that is close to key order (the state
+// stays in the order of the last build and moves by one drift in between).
+// The stable order is the order of the composite (key, current index), so
+// per system: nb - 1 non-decreasing splitters are taken from the last
+// build's sorted keys at regular positions (k_ss_split); each key goes to the
+// bucket of the number of splitters at or below its composite; buckets are laid out back to back
+// (counts, then a scan) and each is sorted by composite in shared memory by
+// one block. Keys end sorted in keys[0] with their source positions in
+// vals[0], exactly as the radix sort leaves them. A bucket of more than
+// SS_CAP keys (a state far from key order) makes the build leave the order
+// unchanged and record ST_SORT; the build is then repeated with the radix
+// sort.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool comp_less(uint64_t ka, uint32_t va, uint64_t kb, uint32_t vb)
+{
+    return ka < kb || (ka == kb && va < vb);
+}
+
+// Block-wide stable LSD radix sort of n keys (with their positions) in shared
+// memory, over the key bits that differ between the smallest and the largest
+// key, 8 bits per pass; equal keys are then put in order of their positions
+// (ties are rare: particles in one cell of the finest level). blockDim.x =
+// SSB_THREADS; whist holds SSB_WARPS x 256 counters; n <= SSB_THREADS * EPT.
+constexpr int SSB_THREADS = 512, SSB_WARPS = SSB_THREADS / 32;
+
+template <int EPT>
+__device__ __forceinline__ void block_radix_sort(uint64_t *sk, uint32_t *sv, int n, uint32_t (*whist)[256],
+                                                 uint32_t *tloc, uint64_t *red)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned ltmask = (1u << lane) - 1u;
+    // the bits that vary: highest set bit of (min key ^ max key)
+    uint64_t mn = ~0ull, mx = 0ull;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        mn = min(mn, sk[j]);
+        mx = max(mx, sk[j]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+        red[w] = mn;
+        red[SSB_WARPS + w] = mx;
+    }
+    __syncthreads();
+    mn = red[0];
+    mx = red[SSB_WARPS];
+    for (int k = 1; k < SSB_WARPS; ++k) {
+        mn = min(mn, red[k]);
+        mx = max(mx, red[SSB_WARPS + k]);
+    }
+    const int vbits = (mn == mx) ? 0 : 64 - __clzll((long long)(mn ^ mx));
+    const int E = (n + SSB_THREADS - 1) / SSB_THREADS;   // slots per thread: every warp holds a share of the keys
+    const int wbase = w * 32 * E;
+    for (int shift = 0; shift < vbits; shift += 8) {
+        uint64_t k[EPT];
+        uint32_t v[EPT], r[EPT], d[EPT];
+        for (int t = threadIdx.x; t < SSB_WARPS * 256; t += blockDim.x) (&whist[0][0])[t] = 0u;
+#pragma unroll
+        for (int it = 0; it < EPT; ++it) {   // warp-striped: (warp, it, lane) is the current order
+            const int e = wbase + it * 32 + lane;
+            const bool ok = it < E && e < n;
+            k[it] = ok ? sk[e] : 0ull;
+            v[it] = ok ? sv[e] : 0u;
+            d[it] = ok ? (uint32_t)(k[it] >> shift) & 0xffu : 256u;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < EPT; ++it) {
+            if (it >= E || wbase + it * 32 >= n) break;   // the rest of this warp's slots are empty
+            const unsigned peers = __match_any_sync(0xffffffffu, d[it]);
+            const uint32_t before = d[it] < 256u ? whist[w][d[it]] : 0u;
+            __syncwarp();
+            if (d[it] < 256u && (peers & ltmask) == 0u) whist[w][d[it]] = before + (uint32_t)__popc(peers);
+            __syncwarp();
+            r[it] = before + (uint32_t)__popc(peers & ltmask);
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {   // per digit: exclusive prefix over the warps, then over the digits
+            const int dd = threadIdx.x;
+            uint32_t run = 0;
+            for (int ww = 0; ww < SSB_WARPS; ++ww) {
+                const uint32_t c = whist[ww][dd];
+                whist[ww][dd] = run;
+                run += c;
+            }
+            uint32_t inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (lane == 31) red[w] = inc;   // the 8 digit warps' totals (red is free here)
+            tloc[dd] = inc - run;
+        }
+        __syncthreads();
+        if (threadIdx.x < 256) {
+            uint32_t pre = 0;
+            for (int ww = 0; ww < w; ++ww) pre += (uint32_t)red[ww];
+            tloc[threadIdx.x] += pre;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < EPT; ++it)
+            if (d[it] < 256u) {
+                const uint32_t pos = tloc[d[it]] + whist[w][d[it]] + r[it];
+                sk[pos] = k[it];
+                sv[pos] = v[it];
+            }
+        __syncthreads();
+    }
+    // runs of equal keys: in order of their positions (insertion sort by the run's first thread)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j + 1 < n && sk[j + 1] == sk[j] && (j == 0 || sk[j - 1] != sk[j])) {
+            int e = j + 1;
+            while (e < n && sk[e] == sk[j]) ++e;
+            for (int a = j + 1; a < e; ++a) {
+                const uint32_t x = sv[a];
+                int b = a - 1;
+                while (b >= j && sv[b] > x) {
+                    sv[b + 1] = sv[b];
+                    --b;
+                }
+                sv[b + 1] = x;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// One block per system: its nb - 1 splitters and cleared bucket counts. It
+// runs before the new keys are computed, on the keys of the last build: the
+// state is still in that build's order and its sorted keys are still in the
+// key buffer, so the composite (old key, position) at position j n / nb is the
+// j-th nb-quantile of the last build, and the particles have moved little
+// since. A running maximum over j makes the splitters non-decreasing whatever
+// the buffer holds (another batch, a first build): buckets may then be empty
+// or large, and a large one sends the build to the radix sort.
+__device__ __forceinline__ void comp_max(uint64_t &k, uint32_t &v, uint64_t k2, uint32_t v2)
+{
+    if (comp_less(k, v, k2, v2)) {
+        k = k2;
+        v = v2;
+    }
+}
+
+__global__ void __launch_bounds__(SSB_THREADS) k_ss_split(const uint64_t *__restrict__ key,
+                                                          const int64_t *__restrict__ off, const SSys *__restrict__ ss,
+                                                          int S, uint64_t *__restrict__ spk, uint32_t *__restrict__ spv,
+                                                          uint32_t *__restrict__ cnt)
+{
+    __shared__ uint64_t wk[SSB_WARPS];
+    __shared__ uint32_t wv[SSB_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int s = blockIdx.x; s < S; s += gridDim.x) {
+        const SSys y = ss[s];
+        const int64_t o = off[s], n = off[s + 1] - off[s];
+        for (int b = threadIdx.x; b < y.nb; b += blockDim.x) cnt[y.bbase + b] = 0u;
+        const int m = y.nb - 1;   // splitters
+        if (m > 0) {
+            // thread t takes candidates [t per, (t + 1) per) and keeps their running maximum
+            const int per = (m + blockDim.x - 1) / blockDim.x;
+            const int j0 = threadIdx.x * per, j1 = min(m, j0 + per);
+            uint64_t rk = 0ull;
+            uint32_t rv = 0u;
+            for (int j = j0; j < j1; ++j) {
+                const int64_t p = o + ((int64_t)(j + 1) * n) / y.nb;   // 1 <= p - o <= n - 1
+                const uint64_t mk = key[p];
+                const uint32_t mv = (uint32_t)p;
+                if (j == j0) {
+                    rk = mk;
+                    rv = mv;
+                } else {
+                    comp_max(rk, rv, mk, mv);
+                }
+                spk[y.bbase + j] = rk;
+                spv[y.bbase + j] = rv;
+            }
+            // exclusive running maximum of the threads' maxima (empty ranges carry the zero composite)
+            uint64_t ik = rk;
+            uint32_t iv = rv;
+#pragma unroll
+            for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                const uint64_t k2 = __shfl_up_sync(0xffffffffu, ik, o2);
+                const uint32_t v2 = __shfl_up_sync(0xffffffffu, iv, o2);
+                if (lane >= o2) comp_max(ik, iv, k2, v2);
+            }
+            if (lane == 31) {
+                wk[w] = ik;
+                wv[w] = iv;
+            }
+            __syncthreads();
+            uint64_t pk = 0ull;
+            uint32_t pv = 0u;
+            for (int ww = 0; ww < w; ++ww) comp_max(pk, pv, wk[ww], wv[ww]);
+            {
+                const uint64_t k2 = __shfl_up_sync(0xffffffffu, ik, 1);
+                const uint32_t v2 = __shfl_up_sync(0xffffffffu, iv, 1);
+                if (lane >= 1) comp_max(pk, pv, k2, v2);
+            }
+            for (int j = j0; j < j1; ++j) {   // apply the maximum of everything before this thread's range
+                uint64_t k2 = spk[y.bbase + j];
+                uint32_t v2 = spv[y.bbase + j];
+                comp_max(k2, v2, pk, pv);
+                spk[y.bbase + j] = k2;
+                spv[y.bbase + j] = v2;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Bucket of every key (the number of its system's splitters at or below its
+// composite), and the bucket counts.
+__global__ void __launch_bounds__(256) k_ss_count(int64_t N, const uint64_t *__restrict__ key,
+                                                  const int32_t *__restrict__ psys, const SSys *__restrict__ ss,
+                                                  const uint64_t *__restrict__ spk, const uint32_t *__restrict__ spv,
+                                                  uint32_t *__restrict__ pb, uint32_t *__restrict__ cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < N; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        uint32_t b = ~0u;
+        if (i < N) {
+            const SSys y = ss[psys[i]];
+            const uint64_t k = key[i];
+            int lo = 0, hi = y.nb - 1;   // upper bound over the splitters [0, nb - 1)
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (comp_less(k, (uint32_t)i, spk[y.bbase + mid], spv[y.bbase + mid])) hi = mid;
+                else lo = mid + 1;
+            }
+            b = (uint32_t)(y.bbase + lo);
+            pb[i] = b;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b != ~0u && lane == __ffs(peers) - 1) atomicAdd(cnt + b, (uint32_t)__popc(peers));
+    }
+}
+
+// One block per system: bucket starts (exclusive scan of the counts from the
+// system's first position) and the overflow check.
+__global__ void __launch_bounds__(256) k_ss_scan(const int64_t *__restrict__ off, const SSys *__restrict__ ss, int S,
+                                                 const uint32_t *__restrict__ cnt, uint32_t *__restrict__ start,
+                                                 uint32_t *__restrict__ cur, uint32_t *flag, Status *st, int where)
+{
+    __shared__ uint32_t part[256];
+    for (int s = blockIdx.x; s < S; s += gridDim.x) {
+        const SSys y = ss[s];
+        const int per = (y.nb + blockDim.x - 1) / blockDim.x;
+        const int b0 = threadIdx.x * per, b1 = min(y.nb, b0 + per);
+        uint32_t sum = 0, mx = 0;
+        for (int b = b0; b < b1; ++b) {
+            const uint32_t v = cnt[y.bbase + b];
+            sum += v;
+            mx = max(mx, v);
+        }
+        part[threadIdx.x] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = (uint32_t)off[s];
+            for (int t = 0; t < (int)blockDim.x; ++t) {
+                const uint32_t v = part[t];
+                part[t] = run;
+                run += v;
+            }
+        }
+        __syncthreads();
+        uint32_t run = part[threadIdx.x];
+        for (int b = b0; b < b1; ++b) {
+            start[y.bbase + b] = run;
+            cur[y.bbase + b] = 0u;
+            run += cnt[y.bbase + b];
+        }
+        if (mx > (uint32_t)SS_CAP) {
+            atomicExch(flag, 1u);
+            fail(st, ST_SORT, where);
+        }
+        __syncthreads();
+    }
+}
+
+// Every key and its position into its bucket's range (any order inside).
+__global__ void __launch_bounds__(256) k_ss_scatter(int64_t N, const uint64_t *__restrict__ k0,
+                                                    const uint32_t *__restrict__ pb, const uint32_t *__restrict__ start,
+                                                    uint32_t *__restrict__ cur, uint64_t *__restrict__ k1,
+                                                    uint32_t *__restrict__ v1, const uint32_t *flag)
+{
+    if (*flag) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned ltmask = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < N; i0 += stride) {
+        const int64_t i = i0 + threadIdx.x;
+        const uint32_t b = i < N ? pb[i] : ~0u;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (b != ~0u && lane == leader) base = atomicAdd(cur + b, (uint32_t)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (b != ~0u) {
+            const uint32_t pos = start[b] + base + (uint32_t)__popc(peers & ltmask);
+            k1[pos] = k0[i];
+            v1[pos] = (uint32_t)i;
+        }
+    }
+}
+
+// One block per bucket: its keys sorted by composite in shared memory, written
+// to their final positions.
+__global__ void __launch_bounds__(SSB_THREADS) k_ss_sort(int nbk, const uint32_t *__restrict__ cnt,
+                                                         const uint32_t *__restrict__ start,
+                                                         const uint64_t *__restrict__ k1, const uint32_t *__restrict__ v1,
+                                                         uint64_t *__restrict__ k0, uint32_t *__restrict__ v0,
+                                                         const uint32_t *flag)
+{
+    extern __shared__ uint64_t ss_smem[];   // SS_CAP keys, then SS_CAP positions
+    __shared__ uint32_t whist[SSB_WARPS][256];
+    __shared__ uint32_t tloc[256];
+    __shared__ uint64_t red[2 * SSB_WARPS];
+    uint64_t *sk = ss_smem;
+    uint32_t *sv = reinterpret_cast<uint32_t *>(ss_smem + SS_CAP);
+    if (*flag) return;
+    for (int b = blockIdx.x; b < nbk; b += gridDim.x) {
+        const int n = (int)cnt[b];
+        const uint32_t s0 = start[b];
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            sk[j] = k1[s0 + j];
+            sv[j] = v1[s0 + j];
+        }
+        __syncthreads();
+        block_radix_sort<SS_CAP / SSB_THREADS>(sk, sv, n, whist, tloc, red);
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            k0[s0 + j] = sk[j];
+            v0[s0 + j] = sv[j];
         }
         __syncthreads();
     }
@@ -1327,12 +1672,33 @@ void launch_keys_sort(hybrid_ctx *c)
     const int64_t N = c->N;
     uint64_t *k0 = (uint64_t *)c->keys[0].p, *k1 = (uint64_t *)c->keys[1].p;
     uint32_t *v0 = (uint32_t *)c->vals[0].p, *v1 = (uint32_t *)c->vals[1].p;
+    const bool sample = c->ss_ok && !c->sort_fallback;
+    const SSys *ss = (const SSys *)c->ss_sys.p;
+    uint64_t *spk = (uint64_t *)c->ss_spk.p;
+    uint32_t *spv = (uint32_t *)c->ss_spv.p, *cnt = (uint32_t *)c->ss_cnt.p;
+    const int64_t *off = (const int64_t *)c->off_dev.p;
+    if (sample) {   // splitters from the last build's sorted keys, before the new keys replace them
+        k_ss_split<<<std::min(c->S, c->nsm * 2), SSB_THREADS, 0, c->st>>>(k0, off, ss, c->S, spk, spv, cnt);
+        c->launches++;
+    }
     k_keys<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const double *)c->x[0].p, (const double *)c->x[1].p,
                                                     (const double *)c->x[2].p, (const int32_t *)c->psys.p, c->S,
                                                     (const unsigned long long *)c->boxmin.p,
                                                     (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0,
                                                     st);
     c->launches++;
+    if (sample) {
+        uint32_t *start = (uint32_t *)c->ss_start.p;
+        uint32_t *cur = (uint32_t *)c->ss_cur.p, *pb = (uint32_t *)c->ss_pb.p, *flag = (uint32_t *)c->ss_flag.p;
+        cudaMemsetAsync(flag, 0, sizeof(uint32_t), c->st);
+        k_ss_count<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, k0, (const int32_t *)c->psys.p, ss, spk, spv, pb, cnt);
+        k_ss_scan<<<std::min(c->S, c->nsm * 4), 256, 0, c->st>>>(off, ss, c->S, cnt, start, cur, flag, st, c->op);
+        k_ss_scatter<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, k0, pb, start, cur, k1, v1, flag);
+        k_ss_sort<<<std::min(c->nbk, c->nsm * 8), SSB_THREADS, (size_t)SS_CAP * 12, c->st>>>(c->nbk, cnt, start, k1,
+                                                                                               v1, k0, v0, flag);
+        c->launches += 4;
+        return;
+    }
     uint32_t *rs = (uint32_t *)c->hist.p;
     uint32_t *counts = rs + RS_HDR, *look = counts + (size_t)2048 * c->S;
     cudaMemsetAsync(rs, 0, ((size_t)RS_HDR + (size_t)2048 * (c->S + c->nchunks)) * sizeof(uint32_t), c->st);
@@ -1527,6 +1893,11 @@ void launch_group_boxes(hybrid_ctx *c)
         (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p, (const int32_t *)c->psys.p,
         (const SysBox *)c->box.p, (double *)c->glo.p, (double *)c->ghi.p, (GroupF *)c->gF.p, st);
     c->launches += 1;
+}
+
+cudaError_t init_tree_kernels()
+{
+    return cudaFuncSetAttribute(k_ss_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, SS_CAP * 12);
 }
 
 void launch_wait_selftest(hybrid_ctx *c, int max_polls)

@@ -69,8 +69,9 @@ constexpr int WALK_SSTK = 1024;   // entries of a warp's stack kept in shared me
 
 __device__ __forceinline__ void fail(Status *st, int code, int where)
 {
-    atomicCAS(&st->code, 0, code);
-    st->where = where;
+    // the first failure wins and keeps its op index: later kernels of the same sequence may fail too (a build
+    // after an unsorted one), and the sequence resumes at the first
+    if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t &total)

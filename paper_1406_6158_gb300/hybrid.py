@@ -27,7 +27,8 @@ EXPORTS = (
     "hybrid_create", "hybrid_destroy", "hybrid_build_tree", "hybrid_soft_force", "hybrid_hard_force",
     "hybrid_kick", "hybrid_drift", "hybrid_step", "hybrid_step_batched", "hybrid_get_perm", "hybrid_sync",
     "hybrid_last_error", "hybrid_tree_info", "hybrid_tree_copy", "hybrid_lists_copy", "hybrid_interactions",
-    "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_energy", "hybrid_energy_noalloc",
+    "hybrid_profile", "hybrid_profile_read", "hybrid_launch_count", "hybrid_sort_fallbacks", "hybrid_energy",
+    "hybrid_energy_noalloc",
     "hybrid_autotune", "hybrid_selftest_wait", "hybrid_server_create", "hybrid_server_destroy", "hybrid_server_submit",
     "hybrid_server_step", "hybrid_server_next", "hybrid_server_used_bytes", "hybrid_server_last_error",
 )
@@ -113,6 +114,8 @@ def load() -> C.CDLL:
     L.hybrid_last_error.restype = C.c_char_p
     L.hybrid_launch_count.argtypes = [ctx]
     L.hybrid_launch_count.restype = C.c_int64
+    L.hybrid_sort_fallbacks.argtypes = [ctx]
+    L.hybrid_sort_fallbacks.restype = C.c_int64
     L.hybrid_server_used_bytes.argtypes = [VP]
     L.hybrid_server_used_bytes.restype = C.c_double
     L.hybrid_server_last_error.argtypes = [VP]
@@ -309,6 +312,10 @@ class Context:
     def hybrid_launch_count(self) -> int:
         return int(self.L.hybrid_launch_count(self.h))
 
+    def hybrid_sort_fallbacks(self) -> int:
+        """Tree builds repeated with the radix sort after a sample-sort bucket overflowed."""
+        return int(self.L.hybrid_sort_fallbacks(self.h))
+
     def hybrid_autotune(self, systems, candidates=None):
         """Runs the autotuner over `systems` (a System or a list); candidates is a
         list of (n_crit, threads_per_group, tile_depth) or None for the built-in
@@ -340,6 +347,12 @@ class Context:
         return T.value, W.value
 
     # ---- inspection ----
+    def tree_info(self):
+        """(nodes, groups) of the last tree build."""
+        nn, ng = C.c_int64(), C.c_int64()
+        self._check("hybrid_tree_info", self.L.hybrid_tree_info(self.h, C.byref(nn), C.byref(ng)))
+        return nn.value, ng.value
+
     def tree(self, n: int) -> dict:
         nn, ng = C.c_int64(), C.c_int64()
         self._check("hybrid_tree_info", self.L.hybrid_tree_info(self.h, C.byref(nn), C.byref(ng)))
@@ -358,19 +371,24 @@ class Context:
         out["glo"], out["ghi"] = out["glo"][:ng], out["ghi"][:ng]
         return out
 
-    def lists(self, ng: int):
+    def lists(self, ng: int, groups=None):
+        """Per-group lists (cells, particles, hard particles) of the last walk; with `groups`, a dict of the
+        selected groups' lists only (the copy from the device is whole either way)."""
         counts = np.zeros(3 * ng, dtype=np.int64)
         self._check("hybrid_lists_copy", self.L.hybrid_lists_copy(self.h, counts.ctypes.data, None, 0))
         tot = int(counts.sum())
         ent = np.zeros(max(tot, 1), dtype=np.int64)
         self._check("hybrid_lists_copy", self.L.hybrid_lists_copy(self.h, counts.ctypes.data, ent.ctypes.data, tot))
         c3 = counts.reshape(-1, 3)
-        res, o = [], 0
-        for g in range(ng):
-            a, b, c = c3[g]
-            res.append((ent[o:o + a].copy(), ent[o + a:o + a + b].copy(), ent[o + a + b:o + a + b + c].copy()))
-            o += a + b + c
-        return res
+        start = np.zeros(ng + 1, dtype=np.int64)
+        np.cumsum(c3.sum(axis=1), out=start[1:])
+
+        def one(g):
+            o, (a, b, c) = start[g], c3[g]
+            return ent[o:o + a].copy(), ent[o + a:o + a + b].copy(), ent[o + a + b:o + a + b + c].copy()
+        if groups is not None:
+            return {int(g): one(int(g)) for g in groups}
+        return [one(g) for g in range(ng)]
 
 
 class Server:

@@ -30,8 +30,13 @@ def test_hbm_stage_fractions():
     gbs = (1 << 24) * 236 * 8 / 22.2e-3 / 1e9
     assert out["sort"]["GB/s"] == pytest.approx(gbs)
     assert out["sort"]["frac_of_measured_hbm"] == pytest.approx(gbs / float(bench.measured_peaks().get("hbm_gbs", 6655.6)))
-    assert out["kick_drift"]["bytes_per_particle_per_launch"] == 108
-    assert bench.hbm_stages(10, 1, {}) == {}
+    assert out["kick_drift"]["bytes_per_particle"] == 108 and out["kick_drift"]["bytes_per_node"] == 0
+    assert "topology" not in out and bench.hbm_stages(10, 1, {}) == {}
+    # with the node count: topology 8 B per particle + 24 B per node, moments 32 B per particle + 96 B per node
+    out = bench.hbm_stages(1000, 2, {"topology": 1.0, "moments": 2.0}, nodes=300)
+    assert out["topology"]["bytes_per_launch"] == 1000 * 8 + 300 * 24
+    assert out["moments"]["bytes_per_launch"] == 1000 * 32 + 300 * 96
+    assert out["moments"]["GB/s"] == pytest.approx((1000 * 32 + 300 * 96) * 2 / 2e-3 / 1e9)
 
 
 def test_fp32_peak():

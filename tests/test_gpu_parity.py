@@ -158,6 +158,92 @@ def test_sort_order_large(H, sizes):
         assert np.array_equal(s.numpy()["id"], perm)
 
 
+def keyed_order(st):
+    lo, L = oracle.root_box(st["x"], st["y"], st["z"])
+    return oracle.stable_sort(oracle.morton_keys(st["x"], st["y"], st["z"], lo, L))
+
+
+def set_positions(s, st):
+    for d in "xyz":
+        s.t[d].copy_(torch.as_tensor(st[d], device="cuda"))
+    torch.cuda.synchronize()
+
+
+def test_sample_sort_close_to_key_order_with_ties(H):
+    # the key sort as it runs from one build to the next: the sample sort takes its splitters from the last
+    # build's sorted keys. After a build on a state in key order, the positions move by a small drift and 1000
+    # particles spread through the array go to 10 points (equal keys far apart in the current order): the next
+    # build takes the sample sort (no fallback) and gives the oracle's stable order and tree.
+    n = 300000
+    st = ics.plummer(n, 90)
+    st = {k: v[keyed_order(st)].copy() for k, v in st.items()}
+    P = plummer_params(n, 1, eps=1 / 256)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_build_tree(s)              # the first build of a context may take the radix sort
+    torch.cuda.synchronize()
+    f0 = ctx.hybrid_sort_fallbacks()
+    assert np.array_equal(s.numpy()["id"], np.arange(n))
+    st1 = {k: v.copy() for k, v in st.items()}
+    for d in "xyz":
+        st1[d] = st1[d] + 1e-3 * st1["v" + d]
+    rng = np.random.default_rng(3)
+    pick = rng.choice(n, 1000, replace=False)
+    pts = rng.normal(size=(10, 3))
+    for k, d in enumerate("xyz"):
+        st1[d][pick] = pts[np.arange(1000) % 10, k]
+    set_positions(s, st1)
+    ctx.hybrid_build_tree(s)
+    torch.cuda.synchronize()
+    assert ctx.hybrid_sort_fallbacks() == f0
+    assert np.array_equal(s.numpy()["id"], keyed_order(st1))
+    T = oracle.Tree(st1["x"], st1["y"], st1["z"], st1["m"], oparams(P))
+    check_tree(T, ctx.tree(n), 1)
+
+
+def test_sample_sort_overflow_falls_back_to_radix(H):
+    # splitters that do not fit the state: after a build on a Plummer sphere (its sorted keys give the next
+    # build's splitters, at positions j n / nb, nb = ceil(n / 2048)), the particles are replaced by a uniform
+    # cube, some of whose buckets hold more than 8192 keys. The build is repeated with the radix sort, which
+    # gives the same stable order; the build after it takes the sample sort again.
+    n = 100000
+    st = ics.plummer(n, 91)
+    st = {k: v[keyed_order(st)].copy() for k, v in st.items()}
+    P = plummer_params(n, 1)
+    ctx = H.Context(P)
+    s = H.System(st, precision=1)
+    ctx.hybrid_build_tree(s)
+    torch.cuda.synchronize()
+    f0 = ctx.hybrid_sort_fallbacks()
+    cube = {k: v.copy() for k, v in st.items()}
+    rng = np.random.default_rng(4)
+    for d in "xyz":
+        cube[d] = rng.uniform(-1.0, 1.0, n)
+    # the precondition, from the splitters' definition: the cube's composites (key, position) against the
+    # Plummer sphere's sorted composites at positions j n / nb
+    nb = (n + 2047) // 2048
+    lo, L = oracle.root_box(st["x"], st["y"], st["z"])
+    ka = np.sort(oracle.morton_keys(st["x"], st["y"], st["z"], lo, L))
+    pos = (np.arange(1, nb) * n) // nb
+    lo, L = oracle.root_box(cube["x"], cube["y"], cube["z"])
+    kb = oracle.morton_keys(cube["x"], cube["y"], cube["z"], lo, L)
+    comp_a = ka[pos].astype(object) * n + pos
+    comp_b = kb.astype(object) * n + np.arange(n)
+    bucket = np.searchsorted(np.array(sorted(comp_a), dtype=object), comp_b, side="right")
+    assert np.bincount(bucket.astype(np.int64)).max() > 8192
+    set_positions(s, cube)
+    ctx.hybrid_build_tree(s)
+    torch.cuda.synchronize()
+    assert ctx.hybrid_sort_fallbacks() == f0 + 1
+    assert np.array_equal(s.numpy()["id"], keyed_order(cube))
+    T = oracle.Tree(cube["x"], cube["y"], cube["z"], cube["m"], oparams(P))
+    check_tree(T, ctx.tree(n), 1)
+    ctx.hybrid_build_tree(s)              # now in key order: the sample sort again
+    torch.cuda.synchronize()
+    assert ctx.hybrid_sort_fallbacks() == f0 + 1
+    assert np.array_equal(s.numpy()["id"], keyed_order(cube))
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 33])
 def test_tiny_and_coincident(H, n):
     st = ics.plummer(max(n, 2), 9)
@@ -554,24 +640,23 @@ def test_c2_full_size_sampled(H):
     assert np.percentile(eh, 99) <= 1e-5
 
 
-def test_large_hernquist_sampled(H):
-    # Hernquist N = 2^21 (seed 2) with the large workload's parameters (eps 1/512, theta 0.4, R1 = 3 eps,
-    # R2 = 6 eps, n_crit 256): radix tiles of 2048 keys, near work items of the large-batch length; forces of
-    # 200 sampled groups against the oracle on the same tree
-    n = 1 << 21
-    st = ics.hernquist(n, 2)
-    eps = 1 / 512
-    P = plummer_params(n, 1, eps=eps, theta=0.4, R1=3 * eps, R2=6 * eps, n_crit=256)
-    ctx = H.Context(P)
-    s = H.System(st, precision=1)
-    ctx.hybrid_build_tree(s)
-    ctx.hybrid_soft_force(s)
-    ctx.hybrid_hard_force(s)
-    out = s.numpy()
-    T = oracle.Tree(out["x"], out["y"], out["z"], out["m"], oparams(P))
-    assert np.array_equal(T.perm, np.arange(n))
-    rng = np.random.default_rng(1)
-    sel = np.sort(rng.choice(T.ng, 200, replace=False))
+def sampled_lists_match(T, gl, ol, sel):
+    """lists_match on the selected groups: gl maps a group to its GPU lists, ol holds the oracle's for sel."""
+    lf = leaf_of(T)
+    flips = 0
+    for g, b in zip(sel, ol):
+        a = gl[g]
+        for k in range(3):
+            A, B = set(a[k].tolist()), set(b[k].tolist())
+            for e in A ^ B:
+                node = e if k == 0 else lf[e]
+                ok = any(near_threshold(T, g, c, k == 2) for c in ancestors(T, node))
+                assert ok, "group %d list %d entry %d differs away from a threshold" % (g, k, e)
+                flips += 1
+    return flips
+
+
+def sampled_forces_ok(T, out, sel):
     a_s, a_h, _, _ = T.forces(groups=sel)
     mask = ~np.isnan(a_s[:, 0])
     g_s = np.stack([out["ax_s"], out["ay_s"], out["az_s"]], 1).astype(np.float64)[mask]
@@ -581,5 +666,94 @@ def test_large_hernquist_sampled(H):
     nz = np.linalg.norm(a_h[mask], axis=1) > 0
     eh = np.linalg.norm(g_h - a_h[mask], axis=1)[nz] / np.linalg.norm(a_h[mask], axis=1)[nz]
     assert np.percentile(eh, 99) <= 1e-5, np.percentile(eh, 99)
+    assert np.all(np.linalg.norm(g_h, axis=1)[~nz] == 0.0)
+
+
+def large_params(n):
+    eps = 1 / 512
+    return plummer_params(n, 1, eps=eps, theta=0.4, R1=3 * eps, R2=6 * eps, n_crit=256)
+
+
+def test_large_hernquist_tree_lists_forces(H):
+    # Hernquist N = 2^21 (seed 2) with the large workload's parameters (eps 1/512, theta 0.4, R1 = 3 eps,
+    # R2 = 6 eps, n_crit 256): radix tiles of 2048 keys and the large-batch item lengths. Keys, sort order,
+    # topology, groups and group boxes bit-exact over the whole tree; soft and hard lists equal as sets (up to
+    # the 1e-6 threshold band) and forces within 1e-5 at p99 on 200 sampled groups
+    n = 1 << 21
+    st = ics.hernquist(n, 2)
+    P = large_params(n)
+    ctx, s, G = gpu_tree(H, st, P)
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], oparams(P))
+    out = s.numpy()
+    assert np.array_equal(out["id"], T.perm)
+    assert np.array_equal(out["x"], T.x) and np.array_equal(out["m"], T.m)
+    check_tree(T, G, 1)
+    del G
+    rng = np.random.default_rng(1)
+    sel = np.sort(rng.choice(T.ng, 200, replace=False))
+    ctx.hybrid_hard_force(s)              # a hard walk: the lists hold the hard neighbours
+    torch.cuda.synchronize()
+    flips_h = sampled_lists_match(T, ctx.lists(T.ng, sel), T.walk(sel, mode=2), sel)
+    ctx.hybrid_soft_force(s)              # a soft walk: the lists hold cells and soft particles
+    torch.cuda.synchronize()
+    gl = ctx.lists(T.ng, sel)
+    ol = T.walk(sel, mode=1)
+    flips_s = sampled_lists_match(T, gl, ol, sel)
+    total = sum(len(b[0]) + len(b[1]) + len(b[2]) for b in ol)
+    assert flips_s + flips_h <= 1e-4 * total
+    del gl
+    sampled_forces_ok(T, s.numpy(), sel)
     ctx.close()
 
+
+def test_large_workload_full_size_tree(H):
+    # the large workload itself: Hernquist N = 2^24 (seed 2). Keys, sort order, topology, groups and group
+    # boxes bit-exact against the oracle's tree of all 2^24 particles; forces on 64 sampled groups
+    n = 1 << 24
+    st = ics.hernquist(n, 2)
+    P = large_params(n)
+    ctx, s, G = gpu_tree(H, st, P)
+    T = oracle.Tree(st["x"], st["y"], st["z"], st["m"], oparams(P))
+    assert np.array_equal(s.numpy()["id"], T.perm)
+    check_tree(T, G, 1)
+    del G, st
+    ctx.hybrid_soft_force(s)
+    ctx.hybrid_hard_force(s)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(2)
+    sampled_forces_ok(T, s.numpy(), np.sort(rng.choice(T.ng, 64, replace=False)))
+    ctx.close()
+
+
+def ragged_batch(prec):
+    sizes = [1500, 3001, 777, 2048]
+    states = [ics.plummer(n, 50 + k) for k, n in enumerate(sizes)]
+    for k, st in enumerate(states):
+        st["id"] = np.arange(sizes[k], dtype=np.int64)
+    per = []
+    for n in sizes:
+        eps = 1 / (4 * n ** (1 / 3))
+        per.append(plummer_params(n, prec, eps=eps, dt_soft=1 / 128, n_hard=4))
+    return sizes, states, per
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_follows_the_oracle(H, prec):
+    # every system of a ragged batch (its own N and eps, one call per step for all of them) against the
+    # oracle run on that system alone, over two soft steps. FP64: positions and velocities within 1e-9. FP32
+    # pairs: a force error of 1e-5 of |a| <= ~2 kicked over 2 dt_s = 1/64 moves v by up to ~3e-7 and x by
+    # ~100 times less, so velocities within 1e-6 and positions within 1e-8
+    sizes, states, per = ragged_batch(prec)
+    ctx = H.Context(per[0])
+    sysb = [H.System(st, precision=prec, params=p) for st, p in zip(states, per)]
+    ctx.hybrid_step_batched(sysb, 2)
+    tol_x, tol_v = (1e-9, 1e-9) if prec == 0 else (1e-8, 1e-6)
+    for st, p, s in zip(states, per, sysb):
+        out = s.numpy()
+        ost = {k: np.array(v, copy=True) for k, v in st.items()}
+        oracle.hybrid_steps(ost, oparams(p), 2)
+        o, q = np.argsort(out["id"]), np.argsort(ost["id"])
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            tol = tol_v if k.startswith("v") else tol_x
+            assert np.max(np.abs(out[k][o] - ost[k][q])) <= tol, (len(st["x"]), k)
+    ctx.close()

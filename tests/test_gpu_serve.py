@@ -2,11 +2,13 @@
 
 A request's result must not depend on the requests it shared batches with:
 bitwise in the FP64 form, to FP32 summation order in the FP32 form. The
-reference for a request is the same server driving that request alone.
+reference for a request is the same server driving that request alone; each
+request of a mix is also held to the FP64 oracle run on it alone.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1406_6158_gb300 import ics
 
 pytestmark = pytest.mark.gpu
@@ -71,6 +73,28 @@ def test_served_equals_alone(H, prec):
         ic = ics.plummer(n, 100 + t)
         assert np.array_equal(b["m"], ic["m"])         # returned in input order
         assert not np.array_equal(b["x"], ic["x"])     # and advanced
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_served_follow_the_oracle(H, prec):
+    # each request of a mix whose members join at different server steps, against the oracle on that request
+    # alone: two soft steps each (n_hard = 2); FP64 within 1e-9, FP32 pairs positions within 1e-8 and
+    # velocities within 1e-6 (a 1e-5 force error kicked over 2 dt_s)
+    reqs = [(0, 3000, 2), (1, 5000, 2), (2, 2000, 2), (3, 4100, 2)]
+    mix, log = drive(H, prec, reqs, arrivals=[0, 1, 1, 2])
+    assert max(a for a, _, _, _ in log) >= 2
+    tol_x, tol_v = (1e-9, 1e-9) if prec == 0 else (1e-8, 1e-6)
+    for t, n, ns in reqs:
+        p = req_params(H, n, prec)
+        ost = ics.plummer(n, 100 + t)
+        ost["id"] = np.arange(n, dtype=np.int64)
+        oracle.hybrid_steps(ost, oracle.Params(G=p.G, eps=p.eps, theta=p.theta, R1=p.R1, R2=p.R2,
+                                               dt_soft=p.dt_soft, a_err=p.a_err, n_hard=p.n_hard, n_leaf=p.n_leaf,
+                                               n_crit=p.n_crit, mac=p.mac), ns)
+        q = np.argsort(ost["id"])
+        for k in ("x", "y", "z", "vx", "vy", "vz"):
+            tol = tol_v if k.startswith("v") else tol_x
+            assert np.max(np.abs(mix[t][k] - ost[k][q])) <= tol, (t, k)
 
 
 def test_admission_by_bytes(H):
