@@ -67,11 +67,12 @@ constexpr int32_t ST_SORT = 101;
 
 // Sample sort of the keys (the usual path once the state is close to key
 // order): per system, nb buckets of about SS_BUCKET keys split by keys taken
-// at regular positions; a bucket of at most SS_CAP keys is sorted in one block
-// (4 times the target: a particle that moved far in the order shifts the
-// splitters around it by up to one bucket).
+// at regular positions; a bucket of at most SS_CAP keys (twice the target:
+// the splitters are the last build's quantiles, and only the particles that
+// crossed a coarse cell boundary since move between buckets) is sorted in one
+// block.
 constexpr int SS_BUCKET = 2048;
-constexpr int SS_CAP = 8192;
+constexpr int SS_CAP = 4096;
 struct SSys {
     int32_t nb;      // buckets of the system
     int32_t bbase;   // index of its first bucket

@@ -677,7 +677,7 @@ __global__ void __launch_bounds__(256) k_ss_scatter(int64_t N, const uint64_t *_
 
 // One block per bucket: its keys sorted by composite in shared memory, written
 // to their final positions.
-__global__ void __launch_bounds__(SSB_THREADS) k_ss_sort(int nbk, const uint32_t *__restrict__ cnt,
+__global__ void __launch_bounds__(SSB_THREADS, 2) k_ss_sort(int nbk, const uint32_t *__restrict__ cnt,
                                                          const uint32_t *__restrict__ start,
                                                          const uint64_t *__restrict__ k1, const uint32_t *__restrict__ v1,
                                                          uint64_t *__restrict__ k0, uint32_t *__restrict__ v0,

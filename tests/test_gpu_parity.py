@@ -204,7 +204,7 @@ def test_sample_sort_close_to_key_order_with_ties(H):
 def test_sample_sort_overflow_falls_back_to_radix(H):
     # splitters that do not fit the state: after a build on a Plummer sphere (its sorted keys give the next
     # build's splitters, at positions j n / nb, nb = ceil(n / 2048)), the particles are replaced by a uniform
-    # cube, some of whose buckets hold more than 8192 keys. The build is repeated with the radix sort, which
+    # cube, some of whose buckets hold more than 4096 keys. The build is repeated with the radix sort, which
     # gives the same stable order; the build after it takes the sample sort again.
     n = 100000
     st = ics.plummer(n, 91)
@@ -230,7 +230,7 @@ def test_sample_sort_overflow_falls_back_to_radix(H):
     comp_a = ka[pos].astype(object) * n + pos
     comp_b = kb.astype(object) * n + np.arange(n)
     bucket = np.searchsorted(np.array(sorted(comp_a), dtype=object), comp_b, side="right")
-    assert np.bincount(bucket.astype(np.int64)).max() > 8192
+    assert np.bincount(bucket.astype(np.int64)).max() > 4096
     set_positions(s, cube)
     ctx.hybrid_build_tree(s)
     torch.cuda.synchronize()
