@@ -327,14 +327,16 @@ hybrid_status setup_batch(hybrid_ctx *c, const hybrid_system *sys, int S, bool n
         }
     }
     c->nchunks = (int)c->h_chunks.size();
-    // sample sort layout: about SS_BUCKET keys per bucket
+    // sample sort layout: about SS_BUCKET keys per bucket, half that on batches of at most 2^20 particles (more
+    // blocks for the bucket sort when the whole batch is a few tens of buckets)
     c->h_ss.resize(S);
     c->nbk = 0;
     c->ss_ok = true;
+    const int64_t bucket = c->N <= ((int64_t)1 << 20) ? SS_BUCKET / 2 : SS_BUCKET;
     for (int s = 0; s < S; ++s) {
         const int64_t n = c->h_off[s + 1] - c->h_off[s];
         SSys &y = c->h_ss[s];
-        y.nb = (int32_t)((n + SS_BUCKET - 1) / SS_BUCKET);
+        y.nb = (int32_t)((n + bucket - 1) / bucket);
         y.bbase = c->nbk;
         c->nbk += y.nb;
     }

@@ -203,9 +203,10 @@ def test_sample_sort_close_to_key_order_with_ties(H):
 
 def test_sample_sort_overflow_falls_back_to_radix(H):
     # splitters that do not fit the state: after a build on a Plummer sphere (its sorted keys give the next
-    # build's splitters, at positions j n / nb, nb = ceil(n / 2048)), the particles are replaced by a uniform
-    # cube, some of whose buckets hold more than 4096 keys. The build is repeated with the radix sort, which
-    # gives the same stable order; the build after it takes the sample sort again.
+    # build's splitters, at positions j n / nb, nb = ceil(n / 1024) on a batch of at most 2^20 particles), the
+    # particles are replaced by a uniform cube, some of whose buckets hold more than 4096 keys. The build is
+    # repeated with the radix sort, which gives the same stable order; the build after it takes the sample sort
+    # again.
     n = 100000
     st = ics.plummer(n, 91)
     st = {k: v[keyed_order(st)].copy() for k, v in st.items()}
@@ -221,7 +222,7 @@ def test_sample_sort_overflow_falls_back_to_radix(H):
         cube[d] = rng.uniform(-1.0, 1.0, n)
     # the precondition, from the splitters' definition: the cube's composites (key, position) against the
     # Plummer sphere's sorted composites at positions j n / nb
-    nb = (n + 2047) // 2048
+    nb = (n + 1023) // 1024
     lo, L = oracle.root_box(st["x"], st["y"], st["z"])
     ka = np.sort(oracle.morton_keys(st["x"], st["y"], st["z"], lo, L))
     pos = (np.arange(1, nb) * n) // nb
