@@ -40,7 +40,7 @@ FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul,
 # DRAM bytes (read + write) of one far-pair launch on this workload, from one ncu capture of the current far
 # kernel for each variant the keys name (n_crit, threads per group, staging depth). Reported as the roofline's
 # traffic only when the autotuner picks one of these variants, else None.
-FAR_TRAFFIC_BYTES = {}
+FAR_TRAFFIC_BYTES = {(128, 32, 2): 57.29e6, (128, 16, 2): 57.32e6}
 CLOCK_INTERVAL_MS = 20
 L2_FLUSH_BYTES = 256 << 20
 ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
@@ -522,8 +522,11 @@ def c3_record(args, steps, warmup, with_cpu=True):
     torch.cuda.set_stream(stream)
     ctx = hybrid.Context(P, stream)
     s = hybrid.System(st, precision=1, ids=False)
-    chosen, _ = ctx.hybrid_autotune(s, [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0),
-                                         (256, 64, 2), (256, 32, 0)])
+    if args.tune == "auto":
+        cands = [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0), (256, 64, 2), (256, 32, 0)]
+    else:                                  # a fixed choice, e.g. to profile the autotuned configuration
+        cands = [tuple(int(v) for v in args.tune.split(","))]
+    chosen, _ = ctx.hybrid_autotune(s, cands)
     ctx.hybrid_step(s, 0)
     nodes, groups = ctx.tree_info()
     for _ in range(warmup):
@@ -747,7 +750,7 @@ def main():
                          "served: the Poisson request stream; large: the 2^24 Hernquist sphere; "
                          "paper: hybrid against normal tree with the paper's parameters")
     ap.add_argument("--tune", default="auto",
-                    help="auto (autotuner) or n_crit,threads_per_group,tile_depth for the single workload")
+                    help="auto (autotuner) or n_crit,threads_per_group,tile_depth for the single and large workloads")
     ap.add_argument("--c4-count", type=int, default=512)
     ap.add_argument("--c5-count", type=int, default=100)
     ap.add_argument("--c5-max-seconds", type=float, default=600.0)
@@ -925,6 +928,10 @@ def main():
     traffic = args.traffic_bytes if args.traffic_bytes is not None else FAR_TRAFFIC_BYTES.get(tuple(chosen))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "traffic_source": ("dram__bytes_read.sum + dram__bytes_write.sum of one far launch of this "
+                                   "variant on this workload, from an ncu capture of the current kernel (mean "
+                                   "of two launches); not measured in this run") if traffic else
+                                  "no capture of the chosen variant",
                 "kernel": "k_pair_f32 far (cells + far particles, soft force)",
                 "peak_note": "FP32 CUDA-core peak: %d SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" %
                              (props.multi_processor_count, sm_max)}
