@@ -448,8 +448,10 @@ def run_c5(args):
 def hbm_stages(n, n_hard, ms, nodes=None):
     """Achieved HBM bandwidth of the memory-bound stages from their live times per soft step and their
     algorithmic bytes (n_hard builds and drift launches per soft step):
-      sort        per particle 36 (keys: x, y, z in, key and index out) + 8 (digit counts) + 8 passes x 24
-                  (key and index in and out)
+      sort        per particle 36 (keys: x, y, z in, key and index out) + 12 (key in, bucket out) + 24 (key and
+                  bucket in, key and index out to the bucket) + 24 (key and index in and out of the bucket sort):
+                  the sample sort the builds take between steps (a build that falls back to the radix sort moves
+                  36 + 8 + 8 x 24; the line reports the fallbacks)
       topology    per particle 8 (sorted key in); per node 24 out (first, count, level, first child, children,
                   parent)
       moments     per particle 32 (FP32 hi/lo position copies in); per node 24 in (the topology) and 72 out (the
@@ -458,7 +460,7 @@ def hbm_stages(n, n_hard, ms, nodes=None):
       kick_drift  per particle 108 (v 24, a 12, x 24 in; v 24, x 24 out)
     nodes: tree nodes of one build (topology and moments are reported only when it is given)."""
     peak = float(measured_peaks().get("hbm_gbs", 6655.6))
-    per = {"sort": (36 + 8 + 8 * 24, 0), "kick_drift": (108, 0)}
+    per = {"sort": (36 + 12 + 24 + 24, 0), "kick_drift": (108, 0)}
     if nodes:
         per["topology"] = (8, 24)
         per["moments"] = (32, 24 + 72)
