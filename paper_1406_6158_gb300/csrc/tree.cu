@@ -124,12 +124,29 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v)
     return x;
 }
 
-__device__ __forceinline__ uint32_t cell_coord(double p, double lo, double scale)
+// d = p - lo rounds once (FP64); the scale is a power of two 2^s, so
+// floor(d 2^s) is taken from the bits of d (d = m 2^e with an integer m):
+// m shifted by e + s, which keeps the FP64 pipe to one operation per axis.
+__device__ __forceinline__ uint32_t cell_coord(double p, double lo, int s)
 {
-    double t = floor(__dmul_rn(__dsub_rn(p, lo), scale));
-    t = t < 0.0 ? 0.0 : t;
-    t = t > (double)((1u << LEVELS) - 1u) ? (double)((1u << LEVELS) - 1u) : t;
-    return (uint32_t)t;
+    const double d = __dsub_rn(p, lo);
+    if (!(d > 0.0)) return 0u;   // zero, or below the root corner
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(d);
+    const int E = (int)((bits >> 52) & 0x7ffu);
+    const unsigned long long frac = bits & ((1ull << 52) - 1ull);
+    const unsigned long long m = E ? (frac | (1ull << 52)) : frac;
+    const int sh = (E ? E : 1) - 1075 + s;   // d 2^s = m 2^sh
+    constexpr unsigned long long QMAX = (1ull << LEVELS) - 1ull;
+    unsigned long long q;
+    if (sh >= 0) q = sh >= 11 ? QMAX : min(m << sh, QMAX);   // m >= 2^52 when normal: past the clamp
+    else q = -sh >= 64 ? 0ull : (m >> -sh);
+    return (uint32_t)min(q, QMAX);
+}
+
+// exponent s of a scale that is an exact power of two (normal)
+__device__ __forceinline__ int pow2_exponent(double scale)
+{
+    return (int)(((unsigned long long)__double_as_longlong(scale) >> 52) & 0x7ffu) - 1023;
 }
 
 // Also finishes the root cubes (from the atomic min/max) and stores them.
@@ -149,9 +166,10 @@ __global__ void __launch_bounds__(256) k_keys(int64_t N, const double *__restric
     (void)st;   // the sort always runs: later kernels rely on a consistent permutation
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const SysBox b = S == 1 ? b1 : make_box(bmin, bmax, psys[i]);
-        const uint32_t qx = cell_coord(x[i], b.lo[0], b.scale);
-        const uint32_t qy = cell_coord(y[i], b.lo[1], b.scale);
-        const uint32_t qz = cell_coord(z[i], b.lo[2], b.scale);
+        const int es = pow2_exponent(b.scale);
+        const uint32_t qx = cell_coord(x[i], b.lo[0], es);
+        const uint32_t qy = cell_coord(y[i], b.lo[1], es);
+        const uint32_t qz = cell_coord(z[i], b.lo[2], es);
         key[i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
         val[i] = (uint32_t)i;
     }
@@ -1601,30 +1619,43 @@ __global__ void __launch_bounds__(256) k_group_box(const int64_t *__restrict__ n
     const int lane = threadIdx.x & 31;
     const int64_t ng = *ngroups;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
-        const uint32_t f = gfirst[g], n = gcount[g];
-        // exact min/max through the order-preserving integer images (no FP64 pipe work)
-        unsigned long long u[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
-        for (uint32_t i = f + lane; i < f + n; i += 32) {
-            const unsigned long long p0 = ord_dbl(x[i]), p1 = ord_dbl(y[i]), p2 = ord_dbl(z[i]);
-            u[0] = min(u[0], p0);
-            u[1] = min(u[1], p1);
-            u[2] = min(u[2], p2);
-            u[3] = max(u[3], p0);
-            u[4] = max(u[4], p1);
-            u[5] = max(u[5], p2);
+    // a warp takes B consecutive groups (B = groups per warp, 1 to 32): their boxes one after the other (all
+    // lanes), then the FP64 finishing of all B at once, lane k for group g0 + k (a one-lane FP64 instruction costs
+    // the FP64 pipe a whole warp's time)
+    const int64_t B = max((int64_t)1, min((int64_t)32, ng / nw));
+    for (int64_t g0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * B; g0 < ng; g0 += nw * B) {
+        const int gn = (int)min(B, ng - g0);
+        unsigned long long mine[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+        for (int k = 0; k < gn; ++k) {
+            const int64_t g = g0 + k;
+            const uint32_t f = gfirst[g], n = gcount[g];
+            // exact min/max through the order-preserving integer images (no FP64 pipe work)
+            unsigned long long u[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+            for (uint32_t i = f + lane; i < f + n; i += 32) {
+                const unsigned long long p0 = ord_dbl(x[i]), p1 = ord_dbl(y[i]), p2 = ord_dbl(z[i]);
+                u[0] = min(u[0], p0);
+                u[1] = min(u[1], p1);
+                u[2] = min(u[2], p2);
+                u[3] = max(u[3], p0);
+                u[4] = max(u[4], p1);
+                u[5] = max(u[5], p2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) u[j] = min(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
+#pragma unroll
+                for (int j = 3; j < 6; ++j) u[j] = max(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
+            }
+            if (lane == k)
+#pragma unroll
+                for (int j = 0; j < 6; ++j) mine[j] = u[j];
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) u[j] = min(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
-#pragma unroll
-            for (int j = 3; j < 6; ++j) u[j] = max(u[j], __shfl_xor_sync(0xffffffffu, u[j], o));
-        }
-        if (lane == 0) {
+        if (lane < gn) {
+            const int64_t g = g0 + lane;
             double v[6];
-            for (int j = 0; j < 6; ++j) v[j] = unord_dbl(u[j]);
-            const SysBox b = box[psys[f]];
+            for (int j = 0; j < 6; ++j) v[j] = unord_dbl(mine[j]);
+            const SysBox b = box[psys[gfirst[g]]];
             float hc[3], lc[3], he[3];
             for (int d = 0; d < 3; ++d) {
                 glo[3 * g + d] = v[d];
