@@ -15,8 +15,13 @@
 // ahead of their use (see the staging ring). A group of n sinks uses
 // lpc = ceil(n / KS) lanes per copy with KS sinks per lane in registers, and
 // copies = 32 / lpc copies of the group split the sources (source j goes to
-// copy j mod copies) and are added at the end. A group with one chunk stores
-// its sums; a group with several adds them atomically into zeroed outputs.
+// copy j mod copies) and are added at the end. In the far kernel, when that
+// leaves many lanes idle (e.g. 72 sinks, KS = 4: 18 lanes, one copy), the
+// sinks are taken in rounds whose lanes per copy are a power of two (64
+// sinks on 2 copies of 16 lanes, then 8 sinks on 16 copies of 2 lanes):
+// each round streams the item's sources again, but no lane idles. A group
+// with one chunk stores its sums; a group with several adds them atomically
+// into zeroed outputs.
 // rsqrtf runs on the CUDA cores: the pair sum is not a dense contraction.
 //
 // FP64 form (the plain form): one warp per group, one sink per lane, plain
@@ -28,6 +33,9 @@ namespace hy {
 namespace {
 
 constexpr int PAIR_THREADS = 128;
+#ifndef FAR_SPLIT_PCT
+#define FAR_SPLIT_PCT 75
+#endif
 constexpr int PAIR_WARPS = PAIR_THREADS / 32;
 constexpr int TILE = 64;
 
@@ -316,11 +324,23 @@ __device__ __forceinline__ void pipeline(const PairArgs &a, const ItemSrc &src, 
     }
 }
 
-// sums of the copies into copy 0, in copy order
+// sums of the copies into copy 0: a butterfly over the copies when they fill the warp (lpc a power of
+// two), else in copy order
 template <int KS>
 __device__ __forceinline__ void reduce_copies(int lane, int copy, int copies, int lpc, float (&x)[KS], float (&y)[KS],
                                               float (&z)[KS])
 {
+    if (copies > 1 && copies * lpc == 32) {
+        for (int o = lpc; o < 32; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < KS; ++k) {
+                x[k] += __shfl_xor_sync(0xffffffffu, x[k], o);
+                y[k] += __shfl_xor_sync(0xffffffffu, y[k], o);
+                z[k] += __shfl_xor_sync(0xffffffffu, z[k], o);
+            }
+        }
+        return;
+    }
     for (int cc = 1; cc < copies; ++cc) {
         const int src = (copy == 0) ? lane + cc * lpc : lane;
 #pragma unroll
@@ -511,12 +531,17 @@ __global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
         const float4 cref = a.phi[first];
         const float crx = cref.x, cry = cref.y, crz = cref.z;
         inter += (unsigned long long)n * (d.e1 - d.e0);
-        const int lpc = n <= 32 * KS ? (n + KS - 1) / KS : 32;
-        const int copies = 32 / lpc;
-        const int copy = lane / lpc, slot = lane - copy * lpc;
-        const bool active = copy < copies;
-        const int per_round = lpc * KS;
-        for (int r0 = 0; r0 < n; r0 += per_round) {
+        for (int r0 = 0, per_round = 0; r0 < n; r0 += per_round) {
+            const int rem = n - r0;
+            int lpc = rem <= 32 * KS ? (rem + KS - 1) / KS : 32;
+            // far kernel: when the copies would leave many sink slots idle (rem * copies below
+            // FAR_SPLIT_PCT % of 32 KS), this round takes a power of two of lanes per copy, which keeps
+            // every slot busy, and leaves the other sinks to the next round
+            if (!NEAR && rem * (32 / lpc) * 100 < FAR_SPLIT_PCT * 32 * KS) lpc = 1 << (31 - __clz(lpc));
+            const int copies = 32 / lpc;
+            const int copy = lane / lpc, slot = lane - copy * lpc;
+            const bool active = copy < copies;
+            per_round = lpc * KS;
             float sx[KS], sy[KS], sz[KS], ax[KS], ay[KS], az[KS], bx[KS], by[KS], bz[KS];
             float shx[KS], shy[KS], shz[KS], slx[KS], sly[KS], slz[KS];
 #pragma unroll
