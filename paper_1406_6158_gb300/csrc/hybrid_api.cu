@@ -395,8 +395,9 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
         launch_kick_seq(c, o.nk, o.which, o.kmode, o.val, o.dmode, o.dval, o.mode == 1);
         break;
     case OP_BUILD: {
-        // The build as a two-branch DAG: after the key sort, the topology and the group table (keys only)
-        // run beside the permutation of the state; then the group boxes beside the moments.
+        // The build as a two-branch DAG: after the key sort, the topology (keys only) and then the group
+        // table run beside the permutation of the state; the moments need the topology and the permuted
+        // state (not the groups), the group boxes the group table and the permuted state.
         cudaEvent_t e0 = nullptr;
         prof_begin(c, PROF_TREE, &e0);
         cudaEvent_t e1 = nullptr;
@@ -411,22 +412,22 @@ void enqueue(hybrid_ctx *c, const Op &o, int idx)
         prof_begin(c, PROF_TOPO, &e1);
         launch_build_levels(c);
         prof_end(c, PROF_TOPO, e1);
+        cudaEventRecord(c->ev_join[0], c->st2);   // topology done
         prof_begin(c, PROF_GROUPS, &e1);
         launch_groups(c);
         prof_end(c, PROF_GROUPS, e1);
-        cudaEventRecord(c->ev_join[0], c->st2);
         c->st = main;
         launch_permute(c);
+        cudaEventRecord(c->ev_fork[1], main);      // permuted state done
         cudaStreamWaitEvent(main, c->ev_join[0], 0);
-        cudaEventRecord(c->ev_fork[1], main);
-        cudaStreamWaitEvent(c->st2, c->ev_fork[1], 0);
-        c->st = c->st2;
-        launch_group_boxes(c);
-        cudaEventRecord(c->ev_join[1], c->st2);
-        c->st = main;
         prof_begin(c, PROF_MOM, &e1);
         launch_moments(c);
         prof_end(c, PROF_MOM, e1);
+        c->st = c->st2;
+        cudaStreamWaitEvent(c->st2, c->ev_fork[1], 0);
+        launch_group_boxes(c);
+        cudaEventRecord(c->ev_join[1], c->st2);
+        c->st = main;
         cudaStreamWaitEvent(main, c->ev_join[1], 0);
         prof_end(c, PROF_TREE, e0);
         break;

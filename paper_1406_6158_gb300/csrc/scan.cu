@@ -1,7 +1,8 @@
 // scan.cu -- exclusive prefix sums whose length may live on the device.
 //
-// Three launches: per-segment sums, one-block scan of the segment sums, and a
-// per-segment block scan that adds the segment offset. The length is read
+// Two launches: per-segment sums, whose last block to finish (a ticket
+// counter, no waiting) also scans the segment sums, and a per-segment block
+// scan that adds the segment offset. The length is read
 // from device memory when the caller has no host copy (tree levels, group
 // counts), so the sequence never waits on the host.
 #include "hy_internal.cuh"
@@ -48,12 +49,16 @@ __device__ __forceinline__ T block_scan_with_total(T v, T &total)
     return r;
 }
 
+// Segment sums; the last block to finish scans them (exclusive, in place) and
+// writes the grand total. Every block takes a ticket, also when the status
+// says to skip the work, so the ticket is back at 0 after every launch.
 template <typename T>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T *data, int64_t n_host, const int64_t *d_n,
-                                                               uint64_t *bsum, const Status *st)
+                                                               uint64_t *bsum, uint64_t *d_total, unsigned *ticket,
+                                                               const Status *st)
 {
-    if (st && st->code) return;
-    const int64_t n = d_n ? *d_n : n_host;
+    const bool skip = st && st->code;
+    const int64_t n = skip ? 0 : (d_n ? *d_n : n_host);
     const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
     for (int64_t s = blockIdx.x; s < nseg; s += gridDim.x) {
         const int64_t base = s * SCAN_SEG + (int64_t)threadIdx.x * SCAN_IPT;
@@ -65,39 +70,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const T *data, int
         block_scan_with_total<uint64_t>(acc, tot);
         if (threadIdx.x == 0) bsum[s] = tot;
     }
-}
-
-// One block: exclusive scan of the segment sums; writes the grand total.
-__global__ void __launch_bounds__(1024) k_scan_spine(uint64_t *bsum, int64_t n_host, const int64_t *d_n,
-                                                     uint64_t *d_total, const Status *st)
-{
-    if (st && st->code) return;
-    const int64_t n = d_n ? *d_n : n_host;
-    const int64_t nseg = (n + SCAN_SEG - 1) / SCAN_SEG;
-    __shared__ uint64_t wsum[32];
-    __shared__ uint64_t carry;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ bool last;
+    __threadfence();   // this block's sums are visible before its ticket
     __syncthreads();
-    for (int64_t b0 = 0; b0 < nseg; b0 += 1024) {
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    uint64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nseg; b0 += SCAN_THREADS) {
         const int64_t i = b0 + threadIdx.x;
-        uint64_t v = (i < nseg) ? bsum[i] : 0;
-        uint64_t inc = warp_incl_scan(v);
-        if (lane == 31) wsum[w] = inc;
-        __syncthreads();
-        if (w == 0) {
-            uint64_t s = wsum[lane];
-            uint64_t si = warp_incl_scan(s);
-            wsum[lane] = si - s;
-        }
-        __syncthreads();
-        const uint64_t c0 = carry;
-        if (i < nseg) bsum[i] = c0 + wsum[w] + inc - v;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = c0 + wsum[w] + inc;
-        __syncthreads();
+        const uint64_t v = i < nseg ? __ldcg(bsum + i) : 0ull;
+        uint64_t tot;
+        const uint64_t ex = block_scan_with_total<uint64_t>(v, tot);
+        if (i < nseg) bsum[i] = carry + ex;
+        carry += tot;
     }
-    if (threadIdx.x == 0 && d_total) *d_total = carry;
+    if (threadIdx.x == 0) {
+        if (d_total && !skip) *d_total = carry;
+        *ticket = 0u;
+    }
 }
 
 template <typename T>
@@ -191,10 +183,10 @@ static void scan_impl(hybrid_ctx *c, T *data, int64_t n_host, const int64_t *d_n
     uint64_t *bs = (uint64_t *)c->blocksum.p;
     const int grid = (int)std::min<int64_t>(nseg_max, (int64_t)c->nsm * 8);
     Status *st = always ? nullptr : status_dev(c);
-    k_scan_reduce<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
-    k_scan_spine<<<1, 1024, 0, c->st>>>(bs, n_host, d_n, d_total, st);
+    unsigned *ticket = (unsigned *)((unsigned long long *)c->counter.p + 13);   // 0 between launches
+    k_scan_reduce<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, d_total, ticket, st);
     k_scan_down<T><<<grid, SCAN_THREADS, 0, c->st>>>(data, n_host, d_n, bs, st);
-    c->launches += 3;
+    c->launches += 2;
 }
 
 void scan_u32(hybrid_ctx *c, uint32_t *data, int64_t n_host, const int64_t *d_n, int64_t n_max, uint64_t *d_total,

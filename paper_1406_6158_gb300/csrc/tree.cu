@@ -596,28 +596,49 @@ __global__ void __launch_bounds__(SSB_THREADS) k_ss_split(const uint64_t *__rest
     }
 }
 
-// Bucket of every key (the number of its system's splitters at or below its
-// composite), and the bucket counts.
-__global__ void __launch_bounds__(256) k_ss_count(int64_t N, const uint64_t *__restrict__ key,
-                                                  const int32_t *__restrict__ psys, const SSys *__restrict__ ss,
-                                                  const uint64_t *__restrict__ spk, const uint32_t *__restrict__ spv,
-                                                  uint32_t *__restrict__ pb, uint32_t *__restrict__ cnt)
+// The sample sort's keys: the key of every particle as k_keys, its bucket (the
+// number of its system's splitters, taken before the keys were replaced, at
+// or below its composite (key, position)), and the bucket counts.
+__global__ void __launch_bounds__(256) k_keys_count(int64_t N, const double *__restrict__ x,
+                                                    const double *__restrict__ y, const double *__restrict__ z,
+                                                    const int32_t *__restrict__ psys, int S,
+                                                    const unsigned long long *__restrict__ bmin,
+                                                    const unsigned long long *__restrict__ bmax,
+                                                    SysBox *__restrict__ boxout, uint64_t *__restrict__ key,
+                                                    uint32_t *__restrict__ val, const SSys *__restrict__ ss,
+                                                    const uint64_t *__restrict__ spk, const uint32_t *__restrict__ spv,
+                                                    uint32_t *__restrict__ pb, uint32_t *__restrict__ cnt)
 {
+    if (blockIdx.x == 0)
+        for (int s = threadIdx.x; s < S; s += blockDim.x) boxout[s] = make_box(bmin, bmax, s);
+    __shared__ SysBox b1;   // single-system batches: the cube computed once per block
+    if (S == 1) {
+        if (threadIdx.x == 0) b1 = make_box(bmin, bmax, 0);
+        __syncthreads();
+    }
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < N; i0 += stride) {
         const int64_t i = i0 + threadIdx.x;
         uint32_t b = ~0u;
         if (i < N) {
-            const SSys y = ss[psys[i]];
-            const uint64_t k = key[i];
-            int lo = 0, hi = y.nb - 1;   // upper bound over the splitters [0, nb - 1)
+            const int sy = S == 1 ? 0 : psys[i];
+            const SysBox bx = S == 1 ? b1 : make_box(bmin, bmax, sy);
+            const int es = pow2_exponent(bx.scale);
+            const uint32_t qx = cell_coord(x[i], bx.lo[0], es);
+            const uint32_t qy = cell_coord(y[i], bx.lo[1], es);
+            const uint32_t qz = cell_coord(z[i], bx.lo[2], es);
+            const uint64_t k = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+            key[i] = k;
+            val[i] = (uint32_t)i;
+            const SSys yy = ss[sy];
+            int lo = 0, hi = yy.nb - 1;   // upper bound over the splitters [0, nb - 1)
             while (lo < hi) {
                 const int mid = (lo + hi) >> 1;
-                if (comp_less(k, (uint32_t)i, spk[y.bbase + mid], spv[y.bbase + mid])) hi = mid;
+                if (comp_less(k, (uint32_t)i, spk[yy.bbase + mid], spv[yy.bbase + mid])) hi = mid;
                 else lo = mid + 1;
             }
-            b = (uint32_t)(y.bbase + lo);
+            b = (uint32_t)(yy.bbase + lo);
             pb[i] = b;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, b);
@@ -1712,17 +1733,14 @@ void launch_keys_sort(hybrid_ctx *c)
         k_ss_split<<<std::min(c->S, c->nsm * 2), SSB_THREADS, 0, c->st>>>(k0, off, ss, c->S, spk, spv, cnt);
         c->launches++;
     }
-    k_keys<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const double *)c->x[0].p, (const double *)c->x[1].p,
-                                                    (const double *)c->x[2].p, (const int32_t *)c->psys.p, c->S,
-                                                    (const unsigned long long *)c->boxmin.p,
-                                                    (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0,
-                                                    st);
-    c->launches++;
     if (sample) {
         uint32_t *start = (uint32_t *)c->ss_start.p;
         uint32_t *cur = (uint32_t *)c->ss_cur.p, *pb = (uint32_t *)c->ss_pb.p, *flag = (uint32_t *)c->ss_flag.p;
         cudaMemsetAsync(flag, 0, sizeof(uint32_t), c->st);
-        k_ss_count<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, k0, (const int32_t *)c->psys.p, ss, spk, spv, pb, cnt);
+        k_keys_count<<<grid_for(c, N, 256), 256, 0, c->st>>>(
+            N, (const double *)c->x[0].p, (const double *)c->x[1].p, (const double *)c->x[2].p,
+            (const int32_t *)c->psys.p, c->S, (const unsigned long long *)c->boxmin.p,
+            (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0, ss, spk, spv, pb, cnt);
         k_ss_scan<<<std::min(c->S, c->nsm * 4), 256, 0, c->st>>>(off, ss, c->S, cnt, start, cur, flag, st, c->op);
         k_ss_scatter<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, k0, pb, start, cur, k1, v1, flag);
         k_ss_sort<<<std::min(c->nbk, c->nsm * 8), SSB_THREADS, (size_t)SS_CAP * 12, c->st>>>(c->nbk, cnt, start, k1,
@@ -1730,6 +1748,12 @@ void launch_keys_sort(hybrid_ctx *c)
         c->launches += 4;
         return;
     }
+    k_keys<<<grid_for(c, N, 256), 256, 0, c->st>>>(N, (const double *)c->x[0].p, (const double *)c->x[1].p,
+                                                    (const double *)c->x[2].p, (const int32_t *)c->psys.p, c->S,
+                                                    (const unsigned long long *)c->boxmin.p,
+                                                    (const unsigned long long *)c->boxmax.p, (SysBox *)c->box.p, k0, v0,
+                                                    st);
+    c->launches++;
     uint32_t *rs = (uint32_t *)c->hist.p;
     uint32_t *counts = rs + RS_HDR, *look = counts + (size_t)2048 * c->S;
     cudaMemsetAsync(rs, 0, ((size_t)RS_HDR + (size_t)2048 * (c->S + c->nchunks)) * sizeof(uint32_t), c->st);
