@@ -40,7 +40,7 @@ FLOPS_PER_INTERACTION = 20          # monopole pair: 3 sub, 3 fma, rsqrt, 3 mul,
 # DRAM bytes (read + write) of one far-pair launch on this workload, from one ncu capture of the current far
 # kernel for each variant the keys name (n_crit, threads per group, staging depth). Reported as the roofline's
 # traffic only when the autotuner picks one of these variants, else None.
-FAR_TRAFFIC_BYTES = {(128, 32, 2): 57.29e6, (128, 16, 2): 57.32e6}
+FAR_TRAFFIC_BYTES = {(128, 32, 2): 57.37e6, (128, 32, 4): 57.31e6}
 CLOCK_INTERVAL_MS = 20
 L2_FLUSH_BYTES = 256 << 20
 ENERGY_MAX_N = 1 << 18              # largest N whose energy the paper comparison evaluates (O(N^2) FP64)
@@ -525,7 +525,8 @@ def c3_record(args, steps, warmup, with_cpu=True):
     ctx = hybrid.Context(P, stream)
     s = hybrid.System(st, precision=1, ids=False)
     if args.tune == "auto":
-        cands = [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0), (256, 64, 2), (256, 32, 0)]
+        cands = [(64, 16, 0), (128, 32, 0), (128, 32, 2), (128, 16, 0), (256, 64, 0), (256, 64, 2), (256, 32, 0),
+                 (512, 128, 0), (512, 64, 0)]
     else:                                  # a fixed choice, e.g. to profile the autotuned configuration
         cands = [tuple(int(v) for v in args.tune.split(","))]
     chosen, _ = ctx.hybrid_autotune(s, cands)
