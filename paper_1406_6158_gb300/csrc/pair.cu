@@ -37,6 +37,9 @@ constexpr int PAIR_THREADS = 128;
 #define FAR_SPLIT_PCT 75
 #endif
 constexpr int PAIR_WARPS = PAIR_THREADS / 32;
+#ifndef NEAR_MIN_BLOCKS
+#define NEAR_MIN_BLOCKS 4
+#endif
 constexpr int TILE = 64;
 
 struct PairArgs {
@@ -502,8 +505,11 @@ __device__ __forceinline__ void exp_tile(const Stage &S, int nt, int copy, int c
 
 // NEAR = false: cells + far particles -> soft. NEAR = true: near particles ->
 // soft (1 - K) and/or hard (K), by SOFT/HARD.
+// The near kernels wait on the latency of their loads (work items, sinks, list
+// entries): they are held to 4 blocks of 128 threads per SM (at most 128
+// registers), one block more than they would use freely.
 template <int KS, bool NEAR, bool SOFT, bool HARD, int NST>
-__global__ void __launch_bounds__(PAIR_THREADS) k_pair_f32(PairArgs a)
+__global__ void __launch_bounds__(PAIR_THREADS, NEAR ? NEAR_MIN_BLOCKS : 0) k_pair_f32(PairArgs a)
 {
     using Stage = WarpStage<NST>;
     __shared__ Stage stages[PAIR_WARPS];
