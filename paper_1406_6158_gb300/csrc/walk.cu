@@ -295,7 +295,10 @@ __device__ __forceinline__ bool emit_items(const WalkArgs &a, int t, uint64_t st
 // FP32 form of the walk in one pass (see the top of the file). The warp's
 // region and open-run state of kind t (0 cells, 1 far, 2 near particles)
 // lives on lane t and is broadcast when needed.
-__global__ void __launch_bounds__(WALK_THREADS, 6) k_walk1(WalkArgs a)
+// MINB blocks per SM: 6 (80 registers) for batches of at most 2^20 particles, whose groups are fewer than the
+// resident warps; 8 (64 registers, a few spilled) above, where more warps hide more of the node loads.
+template <int MINB>
+__global__ void __launch_bounds__(WALK_THREADS, MINB) k_walk1(WalkArgs a)
 {
     Status *st = a.st;
     if (st->code) return;
@@ -548,7 +551,8 @@ void launch_walk(hybrid_ctx *c, int mode)
         cudaMemsetAsync(c->counter.p, 0, sizeof(unsigned long long), c->st);
         cudaMemsetAsync((unsigned long long *)c->counter.p + 10, 0, 3 * sizeof(unsigned long long), c->st);
         a.counter = (unsigned long long *)c->counter.p;
-        k_walk1<<<grid, WALK_THREADS, 0, c->st>>>(a);
+        if (small_job) k_walk1<6><<<grid, WALK_THREADS, 0, c->st>>>(a);
+        else k_walk1<8><<<grid, WALK_THREADS, 0, c->st>>>(a);
         prof_end(c, PROF_WALK, e0);
         c->launches += 1;
         c->last_walk_mode = mode;
