@@ -33,13 +33,9 @@ namespace hy {
 namespace {
 
 constexpr int PAIR_THREADS = 128;
-#ifndef FAR_SPLIT_PCT
-#define FAR_SPLIT_PCT 75
-#endif
+constexpr int FAR_SPLIT_PCT = 75;   // far kernel: a round below this fill of its sink slots is split (see below)
 constexpr int PAIR_WARPS = PAIR_THREADS / 32;
-#ifndef NEAR_MIN_BLOCKS
-#define NEAR_MIN_BLOCKS 4
-#endif
+constexpr int NEAR_MIN_BLOCKS = 4;  // near kernels: resident blocks of PAIR_THREADS per SM (see k_pair_f32)
 constexpr int TILE = 64;
 
 struct PairArgs {
