@@ -107,7 +107,9 @@ typedef struct {
  *          a_err and mac (the other fields are taken from the context); NULL
  *          uses the context's parameters.
  * forces_valid in/out: set to 1 by every call that leaves the accelerations
- *          consistent with the positions, to 0 by hybrid_build_tree. */
+ *          consistent with the positions, to 0 by hybrid_build_tree.
+ * n        particles, n >= 1: a call given an empty system (n < 1), alone or
+ *          in a batch, returns HYBRID_EINVAL before anything is enqueued. */
 typedef struct {
     int64_t n;
     double *x, *y, *z, *vx, *vy, *vz, *m;

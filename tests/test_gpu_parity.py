@@ -245,6 +245,25 @@ def test_sample_sort_overflow_falls_back_to_radix(H):
     assert np.array_equal(s.numpy()["id"], keyed_order(cube))
 
 
+def test_empty_system_refused(H):
+    # an empty system (n = 0) is refused with EINVAL before anything is enqueued, alone and inside a batch, and the
+    # context then steps a real system normally
+    ctx = H.Context(plummer_params(64, 1))
+    empty = H.System({k: np.zeros(0) for k in H.System.FIELDS}, precision=1)
+    other = H.System(ics.plummer(64, 3), precision=1)
+    for call in (lambda: ctx.hybrid_build_tree(empty), lambda: ctx.hybrid_step(empty, 1),
+                 lambda: ctx.hybrid_step_batched([other, empty], 1)):
+        with pytest.raises(H.HybridError) as err:
+            call()
+        assert err.value.code == H.EINVAL
+    s = H.System(ics.plummer(64, 3), precision=1)
+    ctx.hybrid_step(s, 1)
+    torch.cuda.synchronize()
+    out = s.numpy()
+    assert all(np.all(np.isfinite(out[k])) for k in ("x", "vx", "ax_s", "ax_h"))
+    ctx.close()
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 17, 33])
 def test_tiny_and_coincident(H, n):
     st = ics.plummer(max(n, 2), 9)
