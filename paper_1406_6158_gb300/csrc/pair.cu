@@ -518,7 +518,10 @@ __global__ void __launch_bounds__(PAIR_THREADS, NEAR ? NEAR_MIN_BLOCKS : 0) k_pa
     int64_t w = next_item(a.counter, lane);
     while (w < W) {
         const int64_t wn = next_item(a.counter, lane);   // the next item's number arrives while this one runs
-        const WorkItem d = a.items[w];
+        // the near kernel takes its items from the last written to the first, which shortens the end of its
+        // launch (fewer SMs idle while the last items run: 0.353 -> 0.338 ms per soft step at N = 2^17; the same
+        // at 2^24); the far kernel is faster in the walk's order
+        const WorkItem d = a.items[NEAR ? W - 1 - w : w];
         const SysParams &P = a.sp[d.sys];
         HardC H;
         H.eps2 = P.eps2f;
